@@ -1,0 +1,230 @@
+/*
+ * pd.h -- C ABI of the GB300 randomised primal-dual (PD-R) radio-interferometric
+ * imaging library (arXiv:1610.08895, Onose, Carrillo, McEwen & Wiaux).
+ *
+ * The library solves, one iteration at a time, the constrained problem of
+ * Sec. 3 (eq. basic-min-problem):
+ *
+ *     minimise ||Psi^H x||_1  subject to  x >= 0,  ||y_i - Phi_i x||_2 <= eps_i,
+ *
+ * with Algorithm 1 (randomised forward-backward PD). Every operation runs in
+ * hand-written CUDA kernels on one GPU; nothing here falls back to the CPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Images are real, row-major [ny][nx]; pixel (iy, ix) sits at centred
+ *   coordinates (iy - ny/2, ix - nx/2).
+ * - Visibilities are complex (interleaved re, im), in the caller's order
+ *   ("user order") unless stated otherwise.
+ * - Element type follows the plan's precision: PD_F32 -> float / float2 pairs,
+ *   PD_F64 -> double / double2 pairs. Device pointers are typed void*.
+ * - "device" pointers must be device-accessible memory of the current CUDA
+ *   device; "host" pointers are ordinary host memory read during the call.
+ * - The caller owns every buffer it passes. The plan and the state own the
+ *   scratch they allocate and free it in their destroy calls.
+ * - Calls are asynchronous on the given stream (a cudaStream_t, passed as
+ *   void*; NULL = legacy default stream) unless a host output is returned,
+ *   in which case the call synchronises that stream before returning.
+ * - Every entry point returns a pd_status; nothing aborts or throws across the
+ *   ABI. pd_last_error() returns a static description of the last failure on
+ *   the calling thread.
+ */
+#ifndef PD_GB300_H
+#define PD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PD_OK = 0,
+    PD_EINVAL = 1,      /* invalid argument (sizes, ranges, null pointers) */
+    PD_ENOMEM = 2,      /* device or host allocation failed */
+    PD_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    PD_ETIMEOUT = 4,    /* a bounded device wait gave up (status word set) */
+    PD_ENOTCONV = 5,    /* power iteration did not reach its tolerance */
+    PD_ENOTSUP = 6      /* valid but unsupported configuration */
+} pd_status;
+
+typedef enum { PD_F32 = 0, PD_F64 = 1 } pd_precision;
+
+typedef struct pd_plan pd_plan;
+typedef struct pd_state pd_state;
+
+/*
+ * Plan description (host memory, read only during pd_plan_create).
+ *
+ * nx, ny        image size; powers of two in [16, 8192].
+ * osf           oversampling per axis; must be 2 (the paper's k = 4 total,
+ *               Sec. 5 "oversampling ratio k=4"), giving a (2ny) x (2nx) grid.
+ * nvis          number of visibilities M >= 1.
+ * uv            host [nvis][2] doubles (u, v) in radians per pixel, each in
+ *               [-pi, pi). u runs along x (columns), v along y (rows).
+ * nblocks       number of data blocks d in [1, 4096] (eq. data-split).
+ * block_of_vis  host [nvis] int32, block index of each visibility in [0, d).
+ * kernel_width  J, even in [2, 16]: the interpolation kernel of G is J x J
+ *               (Sec. 5 uses 8 x 8).
+ * kb_beta       Kaiser-Bessel shape; 0 selects pi*sqrt((J/2)^2*1.5^2 - 0.8).
+ * nbases        b in [1, 16]; basis_ids host [b]: 0 = Dirac, k = db_k (1..8).
+ * levels        wavelet levels L >= 1 with nx >> L >= 1 and ny >> L >= 1.
+ * precision     PD_F32 (complex64 bulk data, FP64 reductions) or PD_F64.
+ * tile          gridding tile edge in cells (power of two, >= J); 0 = choose.
+ */
+typedef struct {
+    int32_t nx, ny;
+    int32_t osf;
+    int64_t nvis;
+    const double* uv;
+    int32_t nblocks;
+    const int32_t* block_of_vis;
+    int32_t kernel_width;
+    double kb_beta;
+    int32_t nbases;
+    const int32_t* basis_ids;
+    int32_t levels;
+    int32_t precision;
+    int32_t tile;
+} pd_plan_desc;
+
+/*
+ * Build a plan: validate the description, sort the visibilities by gridding
+ * tile and block, derive the Daubechies filters, the deapodisation and twiddle
+ * tables, and allocate the plan's device scratch on the current device.
+ * Sec. 2 (Phi = G F Z), Sec. 3 (data split, Psi). *out receives the plan.
+ * Errors: PD_EINVAL (bad description), PD_ENOMEM, PD_ECUDA.
+ */
+pd_status pd_plan_create(const pd_plan_desc* desc, pd_plan** out);
+pd_status pd_plan_destroy(pd_plan* plan);
+
+/* Static description of the last error on the calling thread (never NULL). */
+const char* pd_last_error(void);
+
+/*
+ * Plan facts, host outputs (any pointer may be NULL):
+ * grid size (Ky, Kx), the Kaiser-Bessel beta in use, the tile edge, the number
+ * of (tile, block) segments and of degridding chunks, and bytes of device
+ * memory the plan holds.
+ */
+pd_status pd_plan_info(const pd_plan* plan, int32_t* ky, int32_t* kx, double* beta,
+                       int32_t* tile, int64_t* nsegments, int64_t* nchunks,
+                       int64_t* device_bytes);
+
+/* Daubechies low-pass filter of basis id k (1..8) as derived by the plan,
+ * written to host h[2k] (largest tap first, sum sqrt(2)). */
+pd_status pd_daubechies_filter(int32_t k, double* h);
+
+/*
+ * y = Phi x = G F Z x (Sec. 2) for `batch` images.
+ * x: device real [batch][ny][nx]; y: device complex [batch][nvis], user order.
+ * Errors: PD_EINVAL (null pointers, batch < 1), PD_ECUDA.
+ */
+pd_status pd_apply_phi(pd_plan* plan, const void* x, void* y, int32_t batch, void* stream);
+
+/*
+ * x = Re(Phi^H y) = Re(Z^T F^H G^T y): the adjoint of Phi as a map from real
+ * images to complex visibilities (used in Alg. 1 step 17).
+ * y: device complex [batch][nvis], user order; x: device real [batch][ny][nx].
+ */
+pd_status pd_apply_phi_adj(pd_plan* plan, const void* y, void* x, int32_t batch, void* stream);
+
+/*
+ * Analysis coeffs = Psi^H x = b^{-1/2} [Psi_1^T x; ...; Psi_b^T x] (Sec. 3).
+ * x: device real [ny][nx]; coeffs: device real [b][ny][nx], each basis in the
+ * packed periodic wavelet layout (coarsest approximation top-left).
+ */
+pd_status pd_apply_psi_adj(pd_plan* plan, const void* x, void* coeffs, void* stream);
+
+/* Synthesis x = Psi coeffs = b^{-1/2} sum_j Psi_j coeffs_j (Sec. 3). */
+pd_status pd_apply_psi(pd_plan* plan, const void* coeffs, void* x, void* stream);
+
+/*
+ * Operator norms by the power method (Sec. 5): ||Phi||_S^2 and ||Psi||_S^2,
+ * the largest eigenvalues of Re(Phi^H Phi) and Psi Psi^H, from the device
+ * start image x0 [ny][nx] (not modified). Norms and the stopping test
+ * |lambda_k - lambda_{k-1}| <= tol * lambda_k are FP64. Host outputs; the call
+ * synchronises `stream`. PD_ENOTCONV if max_iter is reached first (outputs
+ * still hold the last estimate).
+ */
+pd_status pd_operator_norms(pd_plan* plan, const void* x0, int32_t max_iter, double tol,
+                            double* phi_norm2, double* psi_norm2, int32_t* iterations,
+                            void* stream);
+
+/*
+ * Algorithm 1 state: x, x~, s (b packed coefficient sets), s~ = Psi s, the data
+ * duals v (internal order), the gridded dual sum U = G^T v, the block data y and
+ * bounds eps, residual norms for the adaptive probabilities, and the iteration
+ * counter t. Allocated on the current device by pd_state_create.
+ */
+pd_status pd_state_create(pd_plan* plan, pd_state** out);
+pd_status pd_state_destroy(pd_state* st);
+
+/*
+ * Load the measurements and reset the iterate to the paper's start values
+ * (x = x~ = s = v = 0, t = 0). y: device complex [nvis], user order; eps: host
+ * double [nblocks], eps_i > 0. The residual norms used by the adaptive
+ * probabilities start at ||y_i|| (= ||Phi_i x^(0) - y_i||).
+ */
+pd_status pd_state_set_data(pd_plan* plan, pd_state* st, const void* y, const double* eps,
+                            void* stream);
+
+/* Iteration parameters (host memory, read during pd_iterate). */
+typedef struct {
+    double tau, sigma, varsigma;   /* step sizes (Sec. 3 convergence condition) */
+    double kappa;                  /* normalised soft threshold (Alg. 1 step 13) */
+    double psi_norm;               /* ||Psi||_S; the threshold is kappa * psi_norm */
+    uint64_t seed;                 /* key of the counter-based active-set draws */
+    const double* p_block;         /* host [nblocks] selection probabilities in (0, 1] */
+    const double* p_basis;         /* host [nbases] basis probabilities in (0, 1] */
+    int32_t adaptive;              /* 1: p_block from Sec. 4 eq. prob-choice */
+    double adapt_n, adapt_p_min, adapt_p_max;   /* n, p_check, p_hat of eq. prob-choice */
+    int32_t use_graph;             /* 1: capture one iteration in a CUDA graph and replay it */
+} pd_params;
+
+/*
+ * Run `niter` iterations of Algorithm 1 (steps 3-18) on `stream`:
+ * active-set draws (step 3; Philox-4x64-10 keyed by (seed, 0), counter
+ * (t, stream, index, 0)), FZx~ (step 4), degridding and the l2-ball dual update
+ * of active blocks (step 8), gridding of the dual change (step 9), the
+ * soft-threshold dual update of active bases (step 13) and its synthesis
+ * (step 14), and the primal update with positivity and over-relaxation
+ * (steps 17-18). Errors: PD_EINVAL (probabilities outside (0, 1], p_max < n/d,
+ * p_min > n/d), PD_ECUDA.
+ */
+pd_status pd_iterate(pd_plan* plan, pd_state* st, const pd_params* params, int32_t niter,
+                     void* stream);
+
+/* Copies out of the state (device destinations; asynchronous). */
+pd_status pd_state_get_x(const pd_state* st, void* x, void* stream);
+pd_status pd_state_get_x_tilde(const pd_state* st, void* x_tilde, void* stream);
+pd_status pd_state_get_s(const pd_state* st, void* s, void* stream);        /* [b][ny][nx] */
+pd_status pd_state_get_v(const pd_plan* plan, const pd_state* st, void* v, void* stream); /* user order */
+
+/*
+ * Diagnostics of the last iteration, host outputs (synchronises `stream`):
+ * t, ||x^t - x^{t-1}||^2 and ||x^t||^2 (FP64), per-block residual norms
+ * ||G_i b~ - y_i|| of the last iteration each block was active (host
+ * [nblocks], may be NULL), current block probabilities (host [nblocks], may be
+ * NULL) and the activity of the last draw (host int32 [nblocks] and
+ * [nbases], may be NULL).
+ */
+pd_status pd_state_report(const pd_plan* plan, const pd_state* st, int64_t* t, double* dx2,
+                          double* x2, double* res_norm, double* p_block, int32_t* block_active,
+                          int32_t* basis_active, void* stream);
+
+/*
+ * Checkpoint: the full state as one host byte buffer. pd_state_save writes
+ * pd_state_bytes() bytes to host `buf`; pd_state_load restores it (same plan).
+ * The counter-based draws make a resumed run identical to an uninterrupted one.
+ */
+size_t pd_state_bytes(const pd_plan* plan);
+pd_status pd_state_save(const pd_plan* plan, const pd_state* st, void* buf, void* stream);
+pd_status pd_state_load(const pd_plan* plan, pd_state* st, const void* buf, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PD_GB300_H */

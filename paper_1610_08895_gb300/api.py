@@ -1,0 +1,232 @@
+"""Python face of the PD-R CUDA library: Plan and State over torch CUDA tensors.
+
+Marshalling only: shapes and dtypes are checked, pointers and the current
+stream are handed to the C ABI (include/pd.h), and every computation runs in
+the library's kernels. Method names follow the C entry points.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+_REAL = {B.PD_F32: torch.float32, B.PD_F64: torch.float64}
+_CPLX = {B.PD_F32: torch.complex64, B.PD_F64: torch.complex128}
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Plan:
+    """pd_plan_create: image size, oversampling 2, uv points, blocks, kernel width, bases."""
+
+    def __init__(self, nx, ny, uv, block_of_vis, nblocks, kernel_width=8, basis_ids=(0,), levels=1,
+                 precision="f32", tile=0, kb_beta=0.0):
+        B.load()
+        self.nx, self.ny = int(nx), int(ny)
+        self.uv = np.ascontiguousarray(uv, dtype=np.float64)
+        self.block_of_vis = np.ascontiguousarray(block_of_vis, dtype=np.int32)
+        self.nvis = len(self.uv)
+        self.nblocks = int(nblocks)
+        self.basis_ids = np.ascontiguousarray(basis_ids, dtype=np.int32)
+        self.nbases = len(self.basis_ids)
+        self.levels = int(levels)
+        self.prec = {"f32": B.PD_F32, "f64": B.PD_F64}[precision] if isinstance(precision, str) else int(precision)
+        self.real_dtype = _REAL[self.prec]
+        self.cplx_dtype = _CPLX[self.prec]
+        d = B.PdPlanDesc(nx=self.nx, ny=self.ny, osf=2, nvis=self.nvis, uv=self.uv.ctypes.data,
+                         nblocks=self.nblocks, block_of_vis=self.block_of_vis.ctypes.data,
+                         kernel_width=int(kernel_width), kb_beta=float(kb_beta), nbases=self.nbases,
+                         basis_ids=self.basis_ids.ctypes.data, levels=self.levels, precision=self.prec,
+                         tile=int(tile))
+        h = ctypes.c_void_p()
+        B.call("pd_plan_create", ctypes.byref(d), ctypes.byref(h))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        ky, kx, tile = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        beta = ctypes.c_double()
+        ns, nc, nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        B.call("pd_plan_info", self._h, ctypes.byref(ky), ctypes.byref(kx), ctypes.byref(beta),
+               ctypes.byref(tile), ctypes.byref(ns), ctypes.byref(nc), ctypes.byref(nb))
+        return {"ky": ky.value, "kx": kx.value, "beta": beta.value, "tile": tile.value,
+                "nsegments": ns.value, "nchunks": nc.value, "device_bytes": nb.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            B.load().pd_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- operators
+    def pd_apply_phi(self, x, y=None):
+        """y = Phi x for x of shape [ny, nx] or [batch, ny, nx]."""
+        batch = x.shape[0] if x.dim() == 3 else 1
+        _need(x, self.real_dtype, (batch, self.ny, self.nx) if x.dim() == 3 else (self.ny, self.nx), "x")
+        shape = (batch, self.nvis) if x.dim() == 3 else (self.nvis,)
+        if y is None:
+            y = torch.empty(shape, dtype=self.cplx_dtype, device=x.device)
+        _need(y, self.cplx_dtype, shape, "y")
+        B.call("pd_apply_phi", self._h, _ptr(x), _ptr(y), batch, _stream())
+        return y
+
+    def pd_apply_phi_adj(self, y, x=None):
+        """x = Re(Phi^H y) for y of shape [nvis] or [batch, nvis]."""
+        batch = y.shape[0] if y.dim() == 2 else 1
+        _need(y, self.cplx_dtype, (batch, self.nvis) if y.dim() == 2 else (self.nvis,), "y")
+        shape = (batch, self.ny, self.nx) if y.dim() == 2 else (self.ny, self.nx)
+        if x is None:
+            x = torch.empty(shape, dtype=self.real_dtype, device=y.device)
+        _need(x, self.real_dtype, shape, "x")
+        B.call("pd_apply_phi_adj", self._h, _ptr(y), _ptr(x), batch, _stream())
+        return x
+
+    def pd_apply_psi_adj(self, x, coeffs=None):
+        _need(x, self.real_dtype, (self.ny, self.nx), "x")
+        if coeffs is None:
+            coeffs = torch.empty((self.nbases, self.ny, self.nx), dtype=self.real_dtype, device=x.device)
+        _need(coeffs, self.real_dtype, (self.nbases, self.ny, self.nx), "coeffs")
+        B.call("pd_apply_psi_adj", self._h, _ptr(x), _ptr(coeffs), _stream())
+        return coeffs
+
+    def pd_apply_psi(self, coeffs, x=None):
+        _need(coeffs, self.real_dtype, (self.nbases, self.ny, self.nx), "coeffs")
+        if x is None:
+            x = torch.empty((self.ny, self.nx), dtype=self.real_dtype, device=coeffs.device)
+        _need(x, self.real_dtype, (self.ny, self.nx), "x")
+        B.call("pd_apply_psi", self._h, _ptr(coeffs), _ptr(x), _stream())
+        return x
+
+    def pd_operator_norms(self, x0, max_iter=1000, tol=1e-8):
+        """(||Phi||_S^2, ||Psi||_S^2, iterations) by the power method from x0."""
+        _need(x0, self.real_dtype, (self.ny, self.nx), "x0")
+        a, b, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        st = B.load().pd_operator_norms(self._h, _ptr(x0), int(max_iter), float(tol), ctypes.byref(a),
+                                        ctypes.byref(b), ctypes.byref(it), _stream())
+        if st not in (B.PD_OK, B.PD_ENOTCONV):
+            B.check(st, "pd_operator_norms")
+        return a.value, b.value, it.value
+
+
+class State:
+    """Algorithm 1 state (pd_state_create / pd_state_set_data / pd_iterate)."""
+
+    def __init__(self, plan):
+        self.plan = plan
+        h = ctypes.c_void_p()
+        B.call("pd_state_create", plan.handle, ctypes.byref(h))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            B.load().pd_state_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pd_state_set_data(self, y, eps):
+        p = self.plan
+        _need(y, p.cplx_dtype, (p.nvis,), "y")
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        if eps.shape != (p.nblocks,):
+            raise ValueError("eps must have one entry per block")
+        B.call("pd_state_set_data", p.handle, self._h, _ptr(y), eps.ctypes.data, _stream())
+
+    def pd_iterate(self, niter, tau, sigma, varsigma, kappa, psi_norm=1.0, seed=0, p_block=None, p_basis=None,
+                   adaptive=None, use_graph=False):
+        p = self.plan
+        pb = np.ascontiguousarray(np.ones(p.nblocks) if p_block is None else p_block, dtype=np.float64)
+        ps = np.ascontiguousarray(np.ones(p.nbases) if p_basis is None else p_basis, dtype=np.float64)
+        prm = B.PdParams(tau=tau, sigma=sigma, varsigma=varsigma, kappa=kappa, psi_norm=psi_norm, seed=int(seed),
+                         p_block=pb.ctypes.data, p_basis=ps.ctypes.data, adaptive=0, adapt_n=0.0,
+                         adapt_p_min=0.0, adapt_p_max=0.0, use_graph=int(bool(use_graph)))
+        if adaptive is not None:
+            prm.adaptive = 1
+            prm.adapt_n = float(adaptive["n"])
+            prm.adapt_p_min = float(adaptive["p_min"])
+            prm.adapt_p_max = float(adaptive["p_max"])
+        B.call("pd_iterate", p.handle, self._h, ctypes.byref(prm), int(niter), _stream())
+
+    def x(self):
+        p = self.plan
+        out = torch.empty((p.ny, p.nx), dtype=p.real_dtype, device="cuda")
+        B.call("pd_state_get_x", self._h, _ptr(out), _stream())
+        return out
+
+    def x_tilde(self):
+        p = self.plan
+        out = torch.empty((p.ny, p.nx), dtype=p.real_dtype, device="cuda")
+        B.call("pd_state_get_x_tilde", self._h, _ptr(out), _stream())
+        return out
+
+    def s(self):
+        p = self.plan
+        out = torch.empty((p.nbases, p.ny, p.nx), dtype=p.real_dtype, device="cuda")
+        B.call("pd_state_get_s", self._h, _ptr(out), _stream())
+        return out
+
+    def v(self):
+        p = self.plan
+        out = torch.empty((p.nvis,), dtype=p.cplx_dtype, device="cuda")
+        B.call("pd_state_get_v", p.handle, self._h, _ptr(out), _stream())
+        return out
+
+    def report(self):
+        p = self.plan
+        t, dx2, x2 = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        res = np.zeros(p.nblocks)
+        pb = np.zeros(p.nblocks)
+        ba = np.zeros(p.nblocks, dtype=np.int32)
+        sa = np.zeros(p.nbases, dtype=np.int32)
+        B.call("pd_state_report", p.handle, self._h, ctypes.byref(t), ctypes.byref(dx2), ctypes.byref(x2),
+               res.ctypes.data, pb.ctypes.data, ba.ctypes.data, sa.ctypes.data, _stream())
+        return {"t": t.value, "dx2": dx2.value, "x2": x2.value, "res_norm": res, "p_block": pb,
+                "block_active": ba.astype(bool), "basis_active": sa.astype(bool)}
+
+    def save(self):
+        p = self.plan
+        n = B.load().pd_state_bytes(p.handle)
+        buf = np.zeros(n, dtype=np.uint8)
+        B.call("pd_state_save", p.handle, self._h, buf.ctypes.data, _stream())
+        return buf
+
+    def load(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        B.call("pd_state_load", self.plan.handle, self._h, buf.ctypes.data, _stream())
+
+
+def daubechies_filter(k):
+    """Low-pass filter of db_k as derived by the library (host)."""
+    h = np.zeros(2 * k)
+    B.call("pd_daubechies_filter", int(k), h.ctypes.data)
+    return h

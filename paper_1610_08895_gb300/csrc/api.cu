@@ -1,0 +1,693 @@
+// C ABI of the PD-R library (declared in include/pd.h): plan construction (host
+// sorting and tables), the operator entry points, the Algorithm 1 state and the
+// iteration driver with optional CUDA-graph replay.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "host_math.hpp"
+#include "plan.hpp"
+
+using namespace pdgb;
+
+static thread_local std::string g_err = "no error";
+
+static pd_status fail(pd_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CU(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(PD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char* pd_last_error(void) { return g_err.c_str(); }
+
+static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+static int ilog2(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
+
+template <typename T> static cudaError_t dalloc(std::vector<void*>& list, size_t& bytes, T** ptr, size_t count) {
+    size_t nb = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc((void**)ptr, nb);
+    if (e == cudaSuccess) { list.push_back((void*)*ptr); bytes += nb; }
+    return e;
+}
+static cudaError_t dalloc_bytes(std::vector<void*>& list, size_t& bytes, void** ptr, size_t nb) {
+    nb = std::max<size_t>(nb, 16);
+    cudaError_t e = cudaMalloc(ptr, nb);
+    if (e == cudaSuccess) { list.push_back(*ptr); bytes += nb; }
+    return e;
+}
+template <typename T> static cudaError_t upload(T* dst, const std::vector<T>& src) {
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+static std::vector<unsigned char> as_real_bytes(const std::vector<double>& v, int prec) {
+    std::vector<unsigned char> out;
+    if (prec == PD_F64) {
+        out.resize(v.size() * sizeof(double));
+        std::memcpy(out.data(), v.data(), out.size());
+    } else {
+        std::vector<float> f(v.begin(), v.end());
+        out.resize(f.size() * sizeof(float));
+        std::memcpy(out.data(), f.data(), out.size());
+    }
+    return out;
+}
+static cudaError_t upload_real(void* dst, const std::vector<double>& v, int prec) {
+    std::vector<unsigned char> b = as_real_bytes(v, prec);
+    if (b.empty()) return cudaSuccess;
+    return cudaMemcpy(dst, b.data(), b.size(), cudaMemcpyHostToDevice);
+}
+
+static void free_all(std::vector<void*>& list) {
+    for (void* q : list) cudaFree(q);
+    list.clear();
+}
+
+extern "C" pd_status pd_plan_destroy(pd_plan* p) {
+    if (!p) return PD_OK;
+    free_all(p->allocs);
+    delete p;
+    return PD_OK;
+}
+
+extern "C" pd_status pd_daubechies_filter(int32_t k, double* h) {
+    if (k < 1 || k > 8 || !h) return fail(PD_EINVAL, "pd_daubechies_filter: k must be in 1..8 and h non-null");
+    std::vector<double> f = daubechies(k);
+    std::memcpy(h, f.data(), f.size() * sizeof(double));
+    return PD_OK;
+}
+
+static pd_status plan_build(pd_plan* p, const pd_plan_desc* d);
+
+extern "C" pd_status pd_plan_create(const pd_plan_desc* d, pd_plan** out) {
+    if (!d || !out) return fail(PD_EINVAL, "pd_plan_create: null argument");
+    *out = nullptr;
+    pd_plan* p = new pd_plan();
+    pd_status st = plan_build(p, d);
+    if (st != PD_OK) {
+        pd_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return PD_OK;
+}
+
+static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
+    if (!is_pow2(d->nx) || !is_pow2(d->ny) || d->nx < 16 || d->ny < 16 || d->nx > 8192 || d->ny > 8192)
+        return fail(PD_EINVAL, "image sides must be powers of two in [16, 8192]");
+    if (d->osf != 2) return fail(PD_EINVAL, "oversampling per axis must be 2");
+    if (d->nvis < 1 || d->nvis > (int64_t)0x7fffffff) return fail(PD_EINVAL, "nvis must be in [1, 2^31)");
+    if (!d->uv || !d->block_of_vis) return fail(PD_EINVAL, "uv and block_of_vis must be non-null");
+    if (d->nblocks < 1 || d->nblocks > 4096) return fail(PD_EINVAL, "nblocks must be in [1, 4096]");
+    if (d->kernel_width < 2 || d->kernel_width > 16 || (d->kernel_width & 1))
+        return fail(PD_EINVAL, "kernel_width must be even in [2, 16]");
+    if (d->nbases < 1 || d->nbases > MAX_BASES || !d->basis_ids) return fail(PD_EINVAL, "nbases must be in [1, 16]");
+    for (int k = 0; k < d->nbases; ++k)
+        if (d->basis_ids[k] < 0 || d->basis_ids[k] > 8) return fail(PD_EINVAL, "basis ids must be 0 (Dirac) or 1..8");
+    if (d->levels < 1 || (d->nx >> d->levels) < 1 || (d->ny >> d->levels) < 1)
+        return fail(PD_EINVAL, "levels must satisfy 1 <= L and n >> L >= 1");
+    if (d->precision != PD_F32 && d->precision != PD_F64) return fail(PD_EINVAL, "precision must be PD_F32 or PD_F64");
+    if (d->kb_beta < 0) return fail(PD_EINVAL, "kb_beta must be >= 0");
+    if (d->tile != 0 && (!is_pow2(d->tile) || d->tile < d->kernel_width))
+        return fail(PD_EINVAL, "tile must be 0 or a power of two >= kernel_width");
+
+    p->prec = d->precision;
+    p->rsz = p->prec == PD_F64 ? 8 : 4;
+    p->csz = 2 * p->rsz;
+    Geo& g = p->g;
+    g.nx = d->nx; g.ny = d->ny; g.Kx = 2 * d->nx; g.Ky = 2 * d->ny;
+    g.J = d->kernel_width;
+    g.beta = d->kb_beta > 0 ? d->kb_beta : kb_beta_default(g.J);
+    int T = d->tile ? d->tile : 64;
+    while (T > std::min(g.Kx, g.Ky)) T >>= 1;
+    while (T < g.J) T <<= 1;
+    if (T > std::min(g.Kx, g.Ky)) return fail(PD_ENOTSUP, "grid smaller than the kernel width");
+    g.tile = T; g.logT = ilog2(T);
+    g.ntx = g.Kx / T; g.nty = g.Ky / T; g.ntiles = g.ntx * g.nty;
+    g.ext = T + g.J - 1; g.halo_lo = g.J / 2 - 1; g.halo_hi = g.J / 2;
+    g.ring = (g.J - 1) * (g.ext + T);
+    p->M = d->nvis; p->d = d->nblocks; p->b = d->nbases; p->L = d->levels;
+    p->basis_ids.assign(d->basis_ids, d->basis_ids + d->nbases);
+    p->n_wavelet = 0;
+    for (int id : p->basis_ids) p->n_wavelet += id > 0;
+    CU(cudaGetDevice(&p->device));
+    CU(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+
+    // ---- visibilities: base cell, fraction, (tile, block) order
+    const int64_t M = p->M;
+    std::vector<int32_t> bx(M), by(M);
+    std::vector<double> frx(M), fry(M);
+    for (int64_t m = 0; m < M; ++m) {
+        const double u = d->uv[2 * m], v = d->uv[2 * m + 1];
+        if (!(u >= -M_PI && u < M_PI && v >= -M_PI && v < M_PI))
+            return fail(PD_EINVAL, "uv points must lie in [-pi, pi)^2");
+        const int blk = d->block_of_vis[m];
+        if (blk < 0 || blk >= p->d) return fail(PD_EINVAL, "block_of_vis out of range");
+        const double gxv = u * g.Kx / (2.0 * M_PI), gyv = v * g.Ky / (2.0 * M_PI);
+        double flx = std::floor(gxv), fly = std::floor(gyv);
+        double fx = gxv - flx, fy = gyv - fly;
+        // a fraction that rounds to 1 in the working precision moves to the next cell
+        if (p->prec == PD_F32) {
+            if ((float)fx >= 1.0f) { flx += 1.0; fx = 0.0; }
+            if ((float)fy >= 1.0f) { fly += 1.0; fy = 0.0; }
+        }
+        bx[m] = (int32_t)((((int64_t)flx % g.Kx) + g.Kx) % g.Kx);
+        by[m] = (int32_t)((((int64_t)fly % g.Ky) + g.Ky) % g.Ky);
+        frx[m] = fx;
+        fry[m] = fy;
+    }
+    const int64_t nbucket = (int64_t)g.ntiles * p->d;
+    std::vector<int32_t> order(M);
+    {
+        std::vector<int64_t> key(M);
+        for (int64_t m = 0; m < M; ++m) {
+            const int t = (by[m] >> g.logT) * g.ntx + (bx[m] >> g.logT);
+            key[m] = (int64_t)t * p->d + d->block_of_vis[m];
+        }
+        if (nbucket <= (int64_t)1 << 25) {
+            std::vector<int64_t> cnt(nbucket + 1, 0);
+            for (int64_t m = 0; m < M; ++m) cnt[key[m] + 1]++;
+            for (int64_t k = 0; k < nbucket; ++k) cnt[k + 1] += cnt[k];
+            for (int64_t m = 0; m < M; ++m) order[cnt[key[m]]++] = (int32_t)m;
+        } else {
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b2) { return key[a] < key[b2]; });
+        }
+        // segments = runs of equal (tile, block)
+        std::vector<int32_t> seg_start, seg_block, seg_tile;
+        int64_t prev = -1;
+        for (int64_t i = 0; i < M; ++i) {
+            const int64_t k = key[order[i]];
+            if (k != prev) {
+                seg_start.push_back((int32_t)i);
+                seg_block.push_back((int32_t)(k % p->d));
+                seg_tile.push_back((int32_t)(k / p->d));
+                prev = k;
+            }
+        }
+        p->nseg = (int64_t)seg_block.size();
+        seg_start.push_back((int32_t)M);
+        std::vector<int32_t> tile_seg_start(g.ntiles + 1, 0);
+        {
+            int64_t s = 0;
+            for (int t = 0; t <= g.ntiles; ++t) {
+                while (s < p->nseg && seg_tile[s] < t) ++s;
+                tile_seg_start[t] = (int32_t)s;
+            }
+        }
+        // chunks in block-major order
+        std::vector<std::vector<int32_t>> segs_of(p->d);
+        for (int64_t s = 0; s < p->nseg; ++s) segs_of[seg_block[s]].push_back((int32_t)s);
+        std::vector<int32_t> cs, ce, cb, bcs(p->d + 1, 0);
+        for (int i = 0; i < p->d; ++i) {
+            bcs[i] = (int32_t)cs.size();
+            for (int32_t s : segs_of[i])
+                for (int32_t a = seg_start[s]; a < seg_start[s + 1]; a += CHUNK) {
+                    cs.push_back(a);
+                    ce.push_back(std::min(a + CHUNK, seg_start[s + 1]));
+                    cb.push_back(i);
+                }
+        }
+        bcs[p->d] = (int32_t)cs.size();
+        p->nchunk = (int64_t)cs.size();
+        p->h_chunk_block = cb;
+        p->h_block_chunk_start = bcs;
+        p->h_tile_seg_start = tile_seg_start;
+        p->h_seg_block = seg_block;
+
+        auto& A = p->allocs;
+        size_t& B = p->device_bytes;
+#define ALLOC(ptr, count) CU(dalloc(A, B, &(ptr), (count)))
+        ALLOC(p->seg_start, seg_start.size());
+        ALLOC(p->seg_block, seg_block.size());
+        ALLOC(p->tile_seg_start, tile_seg_start.size());
+        ALLOC(p->chunk_start, cs.size());
+        ALLOC(p->chunk_end, ce.size());
+        ALLOC(p->chunk_block, cb.size());
+        ALLOC(p->block_chunk_start, bcs.size());
+        CU(upload(p->seg_start, seg_start));
+        CU(upload(p->seg_block, seg_block));
+        CU(upload(p->tile_seg_start, tile_seg_start));
+        CU(upload(p->chunk_start, cs));
+        CU(upload(p->chunk_end, ce));
+        CU(upload(p->chunk_block, cb));
+        CU(upload(p->block_chunk_start, bcs));
+    }
+    auto& A = p->allocs;
+    size_t& B = p->device_bytes;
+    {
+        std::vector<int32_t> cell(M);
+        std::vector<double> fxs(M), fys(M);
+        for (int64_t i = 0; i < M; ++i) {
+            const int32_t m = order[i];
+            cell[i] = (by[m] << 16) | bx[m];
+            fxs[i] = frx[m];
+            fys[i] = fry[m];
+        }
+        ALLOC(p->cell, M);
+        ALLOC(p->perm, M);
+        CU(dalloc_bytes(A, B, &p->fx, M * p->rsz));
+        CU(dalloc_bytes(A, B, &p->fy, M * p->rsz));
+        CU(upload(p->cell, cell));
+        CU(upload(p->perm, order));
+        CU(upload_real(p->fx, fxs, p->prec));
+        CU(upload_real(p->fy, fys, p->prec));
+    }
+    {
+        std::vector<int32_t> iota_c(p->nchunk), iota_t(g.ntiles);
+        std::iota(iota_c.begin(), iota_c.end(), 0);
+        std::iota(iota_t.begin(), iota_t.end(), 0);
+        std::vector<int32_t> counts = {(int32_t)p->nchunk, g.ntiles};
+        std::vector<int32_t> ob(p->d, 1), obs(p->b, 1), ot(g.ntiles, 1);
+        ALLOC(p->all_chunks, iota_c.size());
+        ALLOC(p->all_tiles, iota_t.size());
+        ALLOC(p->counts_all, 2);
+        ALLOC(p->ones_block, ob.size());
+        ALLOC(p->ones_basis, obs.size());
+        ALLOC(p->tile_ones, ot.size());
+        CU(upload(p->all_chunks, iota_c));
+        CU(upload(p->all_tiles, iota_t));
+        CU(upload(p->counts_all, counts));
+        CU(upload(p->ones_block, ob));
+        CU(upload(p->ones_basis, obs));
+        CU(upload(p->tile_ones, ot));
+    }
+    // ---- tables
+    {
+        CU(dalloc_bytes(A, B, &p->cx, g.nx * p->rsz));
+        CU(dalloc_bytes(A, B, &p->cy, g.ny * p->rsz));
+        CU(dalloc_bytes(A, B, &p->twx, g.Kx * p->csz));
+        CU(dalloc_bytes(A, B, &p->twy, g.Ky * p->csz));
+        CU(upload_real(p->cx, deapodisation(g.nx, g.Kx, g.J, g.beta), p->prec));
+        CU(upload_real(p->cy, deapodisation(g.ny, g.Ky, g.J, g.beta), p->prec));
+        CU(upload_real(p->twx, twiddles(g.Kx), p->prec));
+        CU(upload_real(p->twy, twiddles(g.Ky), p->prec));
+        p->h_filt.assign((size_t)p->b * MAX_FILTER, 0.0);
+        p->h_filt_len.assign(p->b, 0);
+        for (int k = 0; k < p->b; ++k) {
+            const int id = p->basis_ids[k];
+            if (id == 0) continue;
+            std::vector<double> h = daubechies(id);
+            p->h_filt_len[k] = (int)h.size();
+            for (size_t j = 0; j < h.size(); ++j) p->h_filt[(size_t)k * MAX_FILTER + j] = h[j];
+        }
+        CU(dalloc_bytes(A, B, &p->filt, (size_t)p->b * MAX_FILTER * p->rsz));
+        ALLOC(p->filt_len, p->b);
+        CU(upload_real(p->filt, p->h_filt, p->prec));
+        CU(upload(p->filt_len, p->h_filt_len));
+    }
+    // ---- scratch
+    {
+        const size_t K = (size_t)g.Kx * g.Ky, N = (size_t)g.nx * g.ny;
+        CU(dalloc_bytes(A, B, &p->t1, (size_t)g.Kx * g.ny * p->csz));
+        CU(dalloc_bytes(A, B, &p->gridb, K * p->csz));
+        CU(dalloc_bytes(A, B, &p->gridu, K * p->csz));
+        CU(dalloc_bytes(A, B, &p->rbuf, (size_t)M * p->csz));
+        ALLOC(p->chunk_part, 2 * p->nchunk);
+        ALLOC(p->blk_norm, 2 * p->d);
+        CU(dalloc_bytes(A, B, &p->blk_scale, p->d * p->rsz));
+        CU(dalloc_bytes(A, B, &p->ringbuf, (size_t)g.ntiles * g.ring * p->csz));
+        const size_t llsz = (size_t)p->b * (g.ny / 2) * (g.nx / 2) * p->rsz;
+        CU(dalloc_bytes(A, B, &p->ll[0], llsz));
+        CU(dalloc_bytes(A, B, &p->ll[1], llsz));
+        CU(dalloc_bytes(A, B, &p->ds, (size_t)p->b * N * p->rsz));
+        p->red_len = 1024;
+        ALLOC(p->red, p->red_len + 8);
+        CU(cudaMemset(p->ds, 0, (size_t)p->b * N * p->rsz));
+    }
+#undef ALLOC
+    CU(cudaDeviceSynchronize());
+    return PD_OK;
+}
+
+extern "C" pd_status pd_plan_info(const pd_plan* p, int32_t* ky, int32_t* kx, double* beta, int32_t* tile,
+                                  int64_t* nsegments, int64_t* nchunks, int64_t* device_bytes) {
+    if (!p) return fail(PD_EINVAL, "pd_plan_info: null plan");
+    if (ky) *ky = p->g.Ky;
+    if (kx) *kx = p->g.Kx;
+    if (beta) *beta = p->g.beta;
+    if (tile) *tile = p->g.tile;
+    if (nsegments) *nsegments = p->nseg;
+    if (nchunks) *nchunks = p->nchunk;
+    if (device_bytes) *device_bytes = (int64_t)p->device_bytes;
+    return PD_OK;
+}
+
+// ------------------------------------------------------------------ operators
+template <typename R>
+static pd_status apply_phi_t(pd_plan* p, const void* x, void* y, int batch, cudaStream_t s) {
+    const int64_t N = (int64_t)p->g.nx * p->g.ny;
+    for (int k = 0; k < batch; ++k) {
+        CU(fwd_fft<R>(p, (const R*)x + k * N, (cplx_t<R>*)p->gridb, s));
+        CU(degrid_plain<R>(p, (const cplx_t<R>*)p->gridb, (cplx_t<R>*)y + k * p->M, s));
+    }
+    return PD_OK;
+}
+template <typename R>
+static pd_status apply_phi_adj_t(pd_plan* p, const void* y, void* x, int batch, cudaStream_t s) {
+    const int64_t N = (int64_t)p->g.nx * p->g.ny;
+    for (int k = 0; k < batch; ++k) {
+        CU(grid_plain<R>(p, (const cplx_t<R>*)y + k * p->M, (cplx_t<R>*)p->gridu, s));
+        CU(inv_fft<R>(p, (const cplx_t<R>*)p->gridu, (R*)x + k * N, nullptr, s));
+    }
+    return PD_OK;
+}
+
+extern "C" pd_status pd_apply_phi(pd_plan* p, const void* x, void* y, int32_t batch, void* stream) {
+    if (!p || !x || !y || batch < 1) return fail(PD_EINVAL, "pd_apply_phi: null argument or batch < 1");
+    return p->prec == PD_F64 ? apply_phi_t<double>(p, x, y, batch, (cudaStream_t)stream)
+                             : apply_phi_t<float>(p, x, y, batch, (cudaStream_t)stream);
+}
+extern "C" pd_status pd_apply_phi_adj(pd_plan* p, const void* y, void* x, int32_t batch, void* stream) {
+    if (!p || !x || !y || batch < 1) return fail(PD_EINVAL, "pd_apply_phi_adj: null argument or batch < 1");
+    return p->prec == PD_F64 ? apply_phi_adj_t<double>(p, y, x, batch, (cudaStream_t)stream)
+                             : apply_phi_adj_t<float>(p, y, x, batch, (cudaStream_t)stream);
+}
+extern "C" pd_status pd_apply_psi_adj(pd_plan* p, const void* x, void* coeffs, void* stream) {
+    if (!p || !x || !coeffs) return fail(PD_EINVAL, "pd_apply_psi_adj: null argument");
+    if (p->prec == PD_F64) CU(psi_adj_plain<double>(p, (const double*)x, (double*)coeffs, (cudaStream_t)stream));
+    else CU(psi_adj_plain<float>(p, (const float*)x, (float*)coeffs, (cudaStream_t)stream));
+    return PD_OK;
+}
+extern "C" pd_status pd_apply_psi(pd_plan* p, const void* coeffs, void* x, void* stream) {
+    if (!p || !x || !coeffs) return fail(PD_EINVAL, "pd_apply_psi: null argument");
+    if (p->prec == PD_F64) CU(psi_plain<double>(p, (const double*)coeffs, (double*)x, (cudaStream_t)stream));
+    else CU(psi_plain<float>(p, (const float*)coeffs, (float*)x, (cudaStream_t)stream));
+    return PD_OK;
+}
+
+// Power method on a symmetric positive operator given as a callback on device images.
+template <typename R, typename Op>
+static pd_status power_t(pd_plan* p, const R* x0, int max_iter, double tol, R* xa, R* xb, double* dn, Op op,
+                         double* lam_out, int* iters, cudaStream_t s) {
+    const int64_t N = (int64_t)p->g.nx * p->g.ny;
+    double h;
+    CU(norm2<R>(p, x0, N, dn, s));
+    CU(cudaMemcpyAsync(&h, dn, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (!(h > 0)) return fail(PD_EINVAL, "power method: zero start image");
+    CU(scale_copy<R>(x0, xa, N, 1.0 / std::sqrt(h), s));
+    double lam = 0.0, prev = 0.0;
+    for (int k = 1; k <= max_iter; ++k) {
+        pd_status st = op(xa, xb);
+        if (st != PD_OK) return st;
+        CU(norm2<R>(p, xb, N, dn, s));
+        CU(cudaMemcpyAsync(&h, dn, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        lam = std::sqrt(h);
+        *iters = k;
+        if (lam == 0.0) { *lam_out = 0.0; return PD_OK; }
+        CU(scale_copy<R>(xb, xa, N, 1.0 / lam, s));
+        if (std::fabs(lam - prev) <= tol * lam) { *lam_out = lam; return PD_OK; }
+        prev = lam;
+    }
+    *lam_out = lam;
+    return PD_ENOTCONV;
+}
+
+template <typename R>
+static pd_status norms_t(pd_plan* p, const void* x0, int max_iter, double tol, double* phi2, double* psi2,
+                         int* iters, cudaStream_t s) {
+    const int64_t N = (int64_t)p->g.nx * p->g.ny;
+    std::vector<void*> tmp;
+    size_t bytes = 0;
+    R *xa, *xb, *coef;
+    cplx_t<R>* vis;
+    double* dn;
+    auto cleanup = [&]() { free_all(tmp); };
+    if (dalloc(tmp, bytes, &xa, N) || dalloc(tmp, bytes, &xb, N) || dalloc(tmp, bytes, &coef, N * p->b) ||
+        dalloc(tmp, bytes, &vis, p->M) || dalloc(tmp, bytes, &dn, 1)) {
+        cleanup();
+        return fail(PD_ENOMEM, "pd_operator_norms: temporary allocation failed");
+    }
+    int it1 = 0, it2 = 0;
+    double l1 = 0, l2 = 0;
+    pd_status st1 = power_t<R>(p, (const R*)x0, max_iter, tol, xa, xb, dn,
+                               [&](R* a, R* b) {
+                                   pd_status q = apply_phi_t<R>(p, a, vis, 1, s);
+                                   return q != PD_OK ? q : apply_phi_adj_t<R>(p, vis, b, 1, s);
+                               },
+                               &l1, &it1, s);
+    if (st1 != PD_OK && st1 != PD_ENOTCONV) { cleanup(); return st1; }
+    pd_status st2 = power_t<R>(p, (const R*)x0, max_iter, tol, xa, xb, dn,
+                               [&](R* a, R* b) {
+                                   cudaError_t e = psi_adj_plain<R>(p, a, coef, s);
+                                   if (!e) e = psi_plain<R>(p, coef, b, s);
+                                   return e ? fail(PD_ECUDA, cudaGetErrorString(e)) : PD_OK;
+                               },
+                               &l2, &it2, s);
+    cleanup();
+    if (st2 != PD_OK && st2 != PD_ENOTCONV) return st2;
+    if (phi2) *phi2 = l1;
+    if (psi2) *psi2 = l2;
+    if (iters) *iters = std::max(it1, it2);
+    if (st1 == PD_ENOTCONV || st2 == PD_ENOTCONV) return fail(PD_ENOTCONV, "power method: max_iter reached");
+    return PD_OK;
+}
+
+extern "C" pd_status pd_operator_norms(pd_plan* p, const void* x0, int32_t max_iter, double tol, double* phi_norm2,
+                                       double* psi_norm2, int32_t* iterations, void* stream) {
+    if (!p || !x0 || max_iter < 1 || !(tol >= 0)) return fail(PD_EINVAL, "pd_operator_norms: bad argument");
+    int it = 0;
+    pd_status st = p->prec == PD_F64
+                       ? norms_t<double>(p, x0, max_iter, tol, phi_norm2, psi_norm2, &it, (cudaStream_t)stream)
+                       : norms_t<float>(p, x0, max_iter, tol, phi_norm2, psi_norm2, &it, (cudaStream_t)stream);
+    if (iterations) *iterations = it;
+    return st;
+}
+
+// ------------------------------------------------------------------ state
+extern "C" pd_status pd_state_destroy(pd_state* st) {
+    if (!st) return PD_OK;
+    if (st->gexec) cudaGraphExecDestroy(st->gexec);
+    free_all(st->allocs);
+    delete st;
+    return PD_OK;
+}
+
+extern "C" pd_status pd_state_create(pd_plan* p, pd_state** out) {
+    if (!p || !out) return fail(PD_EINVAL, "pd_state_create: null argument");
+    pd_state* st = new pd_state();
+    st->plan = p;
+    auto& A = st->allocs;
+    size_t& B = st->device_bytes;
+    const size_t N = (size_t)p->g.nx * p->g.ny, K = (size_t)p->g.Kx * p->g.Ky;
+    bool ok = !dalloc_bytes(A, B, &st->x, N * p->rsz) && !dalloc_bytes(A, B, &st->xt, N * p->rsz) &&
+              !dalloc_bytes(A, B, &st->s, N * p->b * p->rsz) && !dalloc_bytes(A, B, &st->st, N * p->rsz) &&
+              !dalloc_bytes(A, B, &st->v, p->M * p->csz) && !dalloc_bytes(A, B, &st->u, K * p->csz) &&
+              !dalloc_bytes(A, B, &st->y, p->M * p->csz) && !dalloc(A, B, &st->eps, p->d) &&
+              !dalloc(A, B, &st->res_norm, p->d) && !dalloc(A, B, &st->p_block, p->d) &&
+              !dalloc(A, B, &st->p_basis, p->b) && !dalloc(A, B, &st->block_active, p->d) &&
+              !dalloc(A, B, &st->basis_active, p->b) && !dalloc(A, B, &st->act_chunks, p->nchunk) &&
+              !dalloc(A, B, &st->act_tiles, p->g.ntiles) && !dalloc(A, B, &st->tile_active, p->g.ntiles) &&
+              !dalloc(A, B, &st->counts, 2) && !dalloc(A, B, &st->t, 1) && !dalloc(A, B, &st->diag, 2) &&
+              !dalloc(A, B, &st->prim_part, 2 * (size_t)inv_rows_ctas(p)) && !dalloc(A, B, &st->status, 1);
+    if (!ok) {
+        pd_state_destroy(st);
+        return fail(PD_ENOMEM, "pd_state_create: device allocation failed");
+    }
+    for (void* q : A) cudaMemset(q, 0, 16);
+    CU(cudaMemset(st->x, 0, N * p->rsz));
+    CU(cudaMemset(st->xt, 0, N * p->rsz));
+    CU(cudaMemset(st->s, 0, N * p->b * p->rsz));
+    CU(cudaMemset(st->st, 0, N * p->rsz));
+    CU(cudaMemset(st->v, 0, p->M * p->csz));
+    CU(cudaMemset(st->u, 0, K * p->csz));
+    CU(cudaMemset(st->y, 0, p->M * p->csz));
+    CU(cudaDeviceSynchronize());
+    *out = st;
+    return PD_OK;
+}
+
+extern "C" pd_status pd_state_set_data(pd_plan* p, pd_state* st, const void* y, const double* eps, void* stream) {
+    if (!p || !st || !y || !eps || st->plan != p) return fail(PD_EINVAL, "pd_state_set_data: bad argument");
+    for (int i = 0; i < p->d; ++i)
+        if (!(eps[i] > 0)) return fail(PD_EINVAL, "pd_state_set_data: eps_i must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)p->g.nx * p->g.ny, K = (size_t)p->g.Kx * p->g.Ky;
+    if (p->prec == PD_F64) CU(gather_internal<double>(p, (const double2*)y, (double2*)st->y, s));
+    else CU(gather_internal<float>(p, (const float2*)y, (float2*)st->y, s));
+    CU(cudaMemcpyAsync(st->eps, eps, p->d * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(st->x, 0, N * p->rsz, s));
+    CU(cudaMemsetAsync(st->xt, 0, N * p->rsz, s));
+    CU(cudaMemsetAsync(st->s, 0, N * p->b * p->rsz, s));
+    CU(cudaMemsetAsync(st->st, 0, N * p->rsz, s));
+    CU(cudaMemsetAsync(st->v, 0, p->M * p->csz, s));
+    CU(cudaMemsetAsync(st->u, 0, K * p->csz, s));
+    CU(cudaMemsetAsync(st->t, 0, sizeof(int64_t), s));
+    CU(cudaMemsetAsync(st->diag, 0, 2 * sizeof(double), s));
+    std::vector<double> ones_d(p->d, 1.0), ones_b(p->b, 1.0);
+    CU(cudaMemcpyAsync(st->p_block, ones_d.data(), p->d * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(st->p_basis, ones_b.data(), p->b * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(init_res_norm(p, st, s));
+    CU(cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+template <typename R>
+static cudaError_t enqueue_iteration(pd_plan* p, pd_state* st, const pd_params* prm, cudaStream_t s) {
+    cudaError_t e;
+    SelectArgs sa{prm->seed, prm->adaptive, prm->adapt_n, prm->adapt_p_min, prm->adapt_p_max};
+    if ((e = select_active(p, st, sa, s))) return e;
+    if ((e = fwd_fft<R>(p, (const R*)st->xt, (cplx_t<R>*)p->gridb, s))) return e;
+    DualArgs da{st->y, st->v, st->block_active, st->eps, st->res_norm};
+    if ((e = degrid_dual<R>(p, (const cplx_t<R>*)p->gridb, da, st->act_chunks, st->counts, s))) return e;
+    if ((e = grid_dual<R>(p, da, st->act_tiles, st->counts, st->tile_active, (cplx_t<R>*)st->u, s))) return e;
+    if ((e = sparsity_dual<R>(p, (const R*)st->xt, (R*)st->s, (R*)st->st, st->basis_active,
+                              prm->kappa * prm->psi_norm, s)))
+        return e;
+    PrimalArgs pa{prm->tau, prm->sigma, prm->varsigma, st->x, st->xt, st->st, st->prim_part};
+    if ((e = inv_fft<R>(p, (const cplx_t<R>*)st->u, nullptr, &pa, s))) return e;
+    return primal_finish(p, st, s);
+}
+
+static std::vector<unsigned char> params_key(const pd_plan* p, const pd_params* prm, cudaStream_t s) {
+    std::vector<unsigned char> k;
+    auto put = [&](const void* src, size_t n) {
+        const unsigned char* c = (const unsigned char*)src;
+        k.insert(k.end(), c, c + n);
+    };
+    put(&prm->tau, sizeof(double)); put(&prm->sigma, sizeof(double)); put(&prm->varsigma, sizeof(double));
+    put(&prm->kappa, sizeof(double)); put(&prm->psi_norm, sizeof(double)); put(&prm->seed, sizeof(uint64_t));
+    put(&prm->adaptive, sizeof(int32_t)); put(&prm->adapt_n, sizeof(double));
+    put(&prm->adapt_p_min, sizeof(double)); put(&prm->adapt_p_max, sizeof(double));
+    put(&s, sizeof(s));
+    (void)p;
+    return k;
+}
+
+extern "C" pd_status pd_iterate(pd_plan* p, pd_state* st, const pd_params* prm, int32_t niter, void* stream) {
+    if (!p || !st || !prm || st->plan != p || niter < 0) return fail(PD_EINVAL, "pd_iterate: bad argument");
+    if (!prm->p_basis || (!prm->adaptive && !prm->p_block)) return fail(PD_EINVAL, "pd_iterate: missing probabilities");
+    for (int j = 0; j < p->b; ++j)
+        if (!(prm->p_basis[j] > 0 && prm->p_basis[j] <= 1)) return fail(PD_EINVAL, "p_basis must lie in (0, 1]");
+    if (!prm->adaptive) {
+        for (int i = 0; i < p->d; ++i)
+            if (!(prm->p_block[i] > 0 && prm->p_block[i] <= 1)) return fail(PD_EINVAL, "p_block must lie in (0, 1]");
+    } else {
+        const double nd = prm->adapt_n / p->d;
+        if (!(prm->adapt_n > 0 && prm->adapt_n <= p->d && prm->adapt_p_min >= 0 && prm->adapt_p_min <= nd &&
+              prm->adapt_p_min <= prm->adapt_p_max && prm->adapt_p_max <= 1 && prm->adapt_p_max >= nd))
+            return fail(PD_EINVAL, "adaptive probabilities need 0 <= p_min <= n/d <= p_max <= 1");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!prm->adaptive) CU(cudaMemcpyAsync(st->p_block, prm->p_block, p->d * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(st->p_basis, prm->p_basis, p->b * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (niter == 0) return PD_OK;
+    auto enqueue = [&]() {
+        return p->prec == PD_F64 ? enqueue_iteration<double>(p, st, prm, s) : enqueue_iteration<float>(p, st, prm, s);
+    };
+    if (prm->use_graph) {
+        std::vector<unsigned char> key = params_key(p, prm, s);
+        if (!st->gexec || key != st->gkey) {
+            if (st->gexec) { cudaGraphExecDestroy(st->gexec); st->gexec = nullptr; }
+            // relaxed mode: kernel attribute calls made while enqueueing are allowed
+            CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+            cudaError_t e = enqueue();
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+            if (e) { if (graph) cudaGraphDestroy(graph); return fail(PD_ECUDA, std::string("capture: ") + cudaGetErrorString(e)); }
+            CU(e2);
+            cudaError_t e3 = cudaGraphInstantiate(&st->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            CU(e3);
+            st->gkey = key;
+        }
+        for (int k = 0; k < niter; ++k) CU(cudaGraphLaunch(st->gexec, s));
+    } else {
+        for (int k = 0; k < niter; ++k) CU(enqueue());
+    }
+    return PD_OK;
+}
+
+extern "C" pd_status pd_state_get_x(const pd_state* st, void* x, void* stream) {
+    if (!st || !x) return fail(PD_EINVAL, "pd_state_get_x: null argument");
+    const pd_plan* p = st->plan;
+    CU(cudaMemcpyAsync(x, st->x, (size_t)p->g.nx * p->g.ny * p->rsz, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return PD_OK;
+}
+extern "C" pd_status pd_state_get_x_tilde(const pd_state* st, void* x, void* stream) {
+    if (!st || !x) return fail(PD_EINVAL, "pd_state_get_x_tilde: null argument");
+    const pd_plan* p = st->plan;
+    CU(cudaMemcpyAsync(x, st->xt, (size_t)p->g.nx * p->g.ny * p->rsz, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return PD_OK;
+}
+extern "C" pd_status pd_state_get_s(const pd_state* st, void* s, void* stream) {
+    if (!st || !s) return fail(PD_EINVAL, "pd_state_get_s: null argument");
+    const pd_plan* p = st->plan;
+    CU(cudaMemcpyAsync(s, st->s, (size_t)p->b * p->g.nx * p->g.ny * p->rsz, cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+    return PD_OK;
+}
+extern "C" pd_status pd_state_get_v(const pd_plan* p, const pd_state* st, void* v, void* stream) {
+    if (!p || !st || !v || st->plan != p) return fail(PD_EINVAL, "pd_state_get_v: bad argument");
+    if (p->prec == PD_F64) CU(scatter_user<double>(p, (const double2*)st->v, (double2*)v, (cudaStream_t)stream));
+    else CU(scatter_user<float>(p, (const float2*)st->v, (float2*)v, (cudaStream_t)stream));
+    return PD_OK;
+}
+
+extern "C" pd_status pd_state_report(const pd_plan* p, const pd_state* st, int64_t* t, double* dx2, double* x2,
+                                     double* res_norm, double* p_block, int32_t* block_active, int32_t* basis_active,
+                                     void* stream) {
+    if (!p || !st || st->plan != p) return fail(PD_EINVAL, "pd_state_report: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t th = 0;
+    double dg[2] = {0, 0};
+    CU(cudaMemcpyAsync(&th, st->t, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(dg, st->diag, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (res_norm) CU(cudaMemcpyAsync(res_norm, st->res_norm, p->d * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (p_block) CU(cudaMemcpyAsync(p_block, st->p_block, p->d * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (block_active) CU(cudaMemcpyAsync(block_active, st->block_active, p->d * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (basis_active) CU(cudaMemcpyAsync(basis_active, st->basis_active, p->b * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (t) *t = th;
+    if (dx2) *dx2 = dg[0];
+    if (x2) *x2 = dg[1];
+    return PD_OK;
+}
+
+// checkpoint layout: x, xt, s, st, v, u, y (working precision), eps, res_norm, p_block, p_basis, t
+struct Part { void* dev; size_t bytes; };
+static std::vector<Part> state_parts(const pd_plan* p, const pd_state* st) {
+    const size_t N = (size_t)p->g.nx * p->g.ny, K = (size_t)p->g.Kx * p->g.Ky;
+    return {{st->x, N * p->rsz}, {st->xt, N * p->rsz}, {st->s, N * p->b * p->rsz}, {st->st, N * p->rsz},
+            {st->v, p->M * p->csz}, {st->u, K * p->csz}, {st->y, p->M * p->csz}, {st->eps, p->d * sizeof(double)},
+            {st->res_norm, p->d * sizeof(double)}, {st->p_block, p->d * sizeof(double)},
+            {st->p_basis, p->b * sizeof(double)}, {st->t, sizeof(int64_t)}};
+}
+extern "C" size_t pd_state_bytes(const pd_plan* p) {
+    if (!p) return 0;
+    pd_state dummy;
+    size_t n = 0;
+    for (const Part& q : state_parts(p, &dummy)) n += q.bytes;
+    return n;
+}
+extern "C" pd_status pd_state_save(const pd_plan* p, const pd_state* st, void* buf, void* stream) {
+    if (!p || !st || !buf || st->plan != p) return fail(PD_EINVAL, "pd_state_save: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* c = (unsigned char*)buf;
+    for (const Part& q : state_parts(p, st)) {
+        CU(cudaMemcpyAsync(c, q.dev, q.bytes, cudaMemcpyDeviceToHost, s));
+        c += q.bytes;
+    }
+    CU(cudaStreamSynchronize(s));
+    return PD_OK;
+}
+extern "C" pd_status pd_state_load(const pd_plan* p, pd_state* st, const void* buf, void* stream) {
+    if (!p || !st || !buf || st->plan != p) return fail(PD_EINVAL, "pd_state_load: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned char* c = (const unsigned char*)buf;
+    for (const Part& q : state_parts(p, st)) {
+        CU(cudaMemcpyAsync(q.dev, c, q.bytes, cudaMemcpyHostToDevice, s));
+        c += q.bytes;
+    }
+    CU(cudaStreamSynchronize(s));
+    return PD_OK;
+}

@@ -1,0 +1,286 @@
+// Small device-resident steps of Algorithm 1: the active-set draws (step 3) with
+// the optional adaptive probabilities (Sec. 4, eq. prob-choice), the compaction of
+// the active work lists for the persistent degridding/gridding launches, FP64
+// reductions, and index permutations between user and internal visibility order.
+#include <algorithm>
+
+#include "common.cuh"
+#include "plan.hpp"
+
+namespace pdgb {
+
+constexpr int SEL_NT = 1024;
+
+// Exclusive scan of per-thread counts over a 1024-thread block; returns the total.
+__device__ int block_excl_scan(int v, int* sh, int& excl) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = sh[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    const int before = warp > 0 ? sh[warp - 1] : 0;
+    excl = before + x - v;
+    const int total = sh[31];
+    __syncthreads();
+    return total;
+}
+
+// Step 3: Philox draws u(seed, t, stream, index) < p for blocks (stream 0) and
+// bases (stream 1); with adaptive = 1 the block probabilities are first set by
+// eq. (prob-choice) from the current residual norms. Then the active degridding
+// chunks (block-major) and the tiles holding a visibility of an active block are
+// compacted into the lists read by the persistent kernels.
+__global__ void __launch_bounds__(SEL_NT) k_select(
+    uint64_t seed, int adaptive, double an, double pmin, double pmax, int64_t* __restrict__ tptr,
+    double* __restrict__ p_block, const double* __restrict__ p_basis, const double* __restrict__ res_norm,
+    const double* __restrict__ eps, int d, int b, int32_t* __restrict__ block_active,
+    int32_t* __restrict__ basis_active, const int32_t* __restrict__ block_chunk_start, int32_t* __restrict__ act_chunks,
+    const int32_t* __restrict__ tile_seg_start, const int32_t* __restrict__ seg_block, int ntiles,
+    int32_t* __restrict__ tile_active, int32_t* __restrict__ act_tiles, int32_t* __restrict__ counts) {
+    __shared__ int shi[32];
+    __shared__ double shd[32];
+    __shared__ double q_sh, cap_sh;
+    __shared__ int64_t t_sh;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        const int64_t t = *tptr + 1;
+        *tptr = t;
+        t_sh = t;
+    }
+    if (adaptive) {
+        // c_i = max(||r_i|| - eps_i, 0)^2 / eps_i^2; p_i = p_min + min(q_i + a, p_max - p_min)
+        double csum = 0.0;
+        for (int i = tid; i < d; i += SEL_NT) {
+            const double e = eps[i], r = res_norm[i];
+            const double c = r > e ? (r - e) * (r - e) / (e * e) : 0.0;
+            csum += c;
+        }
+        csum = block_sum(csum, shd);
+        if (tid == 0) shd[0] = csum;
+        __syncthreads();
+        csum = shd[0];
+        __syncthreads();
+        const double cap = pmax - pmin;
+        const double target = an - d * pmin;
+        if (csum == 0.0) {
+            for (int i = tid; i < d; i += SEL_NT) p_block[i] = an / d;
+        } else {
+            const double qs = target / csum;
+            // a = 0 unless some q_i exceeds the cap (then some p_i saturates at p_max)
+            int sat = 0;
+            for (int i = tid; i < d; i += SEL_NT) {
+                const double e = eps[i], r = res_norm[i];
+                const double c = r > e ? (r - e) * (r - e) / (e * e) : 0.0;
+                sat |= (qs * c > cap);
+            }
+            sat = __syncthreads_or(sat);
+            double lo = 0.0, hi = 0.0;
+            if (sat) {
+                // f(a) = sum min(q_i + a, cap) is non-decreasing: bisection to double precision
+                hi = cap;
+                for (int it = 0; it < 80; ++it) {
+                    const double mid = 0.5 * (lo + hi);
+                    double f = 0.0;
+                    for (int i = tid; i < d; i += SEL_NT) {
+                        const double e = eps[i], r = res_norm[i];
+                        const double c = r > e ? (r - e) * (r - e) / (e * e) : 0.0;
+                        f += fmin(qs * c + mid, cap);
+                    }
+                    f = block_sum(f, shd);
+                    if (tid == 0) shd[0] = f;
+                    __syncthreads();
+                    f = shd[0];
+                    __syncthreads();
+                    if (f < target) lo = mid; else hi = mid;
+                }
+            }
+            if (tid == 0) { q_sh = qs; cap_sh = hi; }
+            __syncthreads();
+            const double a = cap_sh;
+            for (int i = tid; i < d; i += SEL_NT) {
+                const double e = eps[i], r = res_norm[i];
+                const double c = r > e ? (r - e) * (r - e) / (e * e) : 0.0;
+                p_block[i] = pmin + fmin(q_sh * c + a, cap);
+            }
+        }
+    }
+    __syncthreads();
+    const int64_t t = t_sh;
+    for (int i = tid; i < d; i += SEL_NT) block_active[i] = philox_uniform(seed, (uint64_t)t, 0, i) < p_block[i];
+    for (int j = tid; j < b; j += SEL_NT) basis_active[j] = philox_uniform(seed, (uint64_t)t, 1, j) < p_basis[j];
+    __syncthreads();
+    // active chunks, block-major: each thread owns a contiguous range of blocks
+    {
+        const int per = (d + SEL_NT - 1) / SEL_NT;
+        const int i0 = min(d, tid * per), i1 = min(d, i0 + per);
+        int mine = 0;
+        for (int i = i0; i < i1; ++i)
+            if (block_active[i]) mine += block_chunk_start[i + 1] - block_chunk_start[i];
+        int excl;
+        const int total = block_excl_scan(mine, shi, excl);
+        for (int i = i0; i < i1; ++i) {
+            if (!block_active[i]) continue;
+            for (int c = block_chunk_start[i]; c < block_chunk_start[i + 1]; ++c) act_chunks[excl++] = c;
+        }
+        if (tid == 0) counts[0] = total;
+    }
+    // active tiles
+    {
+        const int per = (ntiles + SEL_NT - 1) / SEL_NT;
+        const int t0 = min(ntiles, tid * per), t1 = min(ntiles, t0 + per);
+        int mine = 0;
+        for (int tt = t0; tt < t1; ++tt) {
+            int on = 0;
+            for (int sg = tile_seg_start[tt]; sg < tile_seg_start[tt + 1]; ++sg) on |= block_active[seg_block[sg]];
+            tile_active[tt] = on;
+            mine += on;
+        }
+        int excl;
+        const int total = block_excl_scan(mine, shi, excl);
+        for (int tt = t0; tt < t1; ++tt)
+            if (tile_active[tt]) act_tiles[excl++] = tt;
+        if (tid == 0) counts[1] = total;
+    }
+}
+
+cudaError_t select_active(const pd_plan* p, pd_state* st, const SelectArgs& a, cudaStream_t s) {
+    k_select<<<1, SEL_NT, 0, s>>>(a.seed, a.adaptive, a.n, a.p_min, a.p_max, st->t, st->p_block, st->p_basis,
+                                 st->res_norm, st->eps, p->d, p->b, st->block_active, st->basis_active,
+                                 p->block_chunk_start, st->act_chunks, p->tile_seg_start, p->seg_block, p->g.ntiles,
+                                 st->tile_active, st->act_tiles, st->counts);
+    return cudaGetLastError();
+}
+
+// Fixed-order sum of per-CTA partials of the primal update: ||x^t - x^{t-1}||^2, ||x^t||^2.
+__global__ void k_sum_pairs(const double* __restrict__ part, int n, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { a += part[2 * i]; b += part[2 * i + 1]; }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) { out[0] = a; out[1] = b; }
+}
+
+cudaError_t primal_finish(const pd_plan* p, pd_state* st, cudaStream_t s) {
+    k_sum_pairs<<<1, 256, 0, s>>>(st->prim_part, inv_rows_ctas(p), st->diag);
+    return cudaGetLastError();
+}
+
+// Deterministic two-level FP64 sum of squares.
+template <typename R>
+__global__ void k_sq_part(const R* __restrict__ x, int64_t n, double* __restrict__ part) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a += (double)x[i] * (double)x[i];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+__global__ void k_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) *out = a;
+}
+
+template <typename R>
+cudaError_t norm2(const pd_plan* p, const R* x, int64_t n, double* out, cudaStream_t s) {
+    const int ctas = std::min<int64_t>(p->red_len, std::max<int64_t>(1, (n + 255) / 256));
+    k_sq_part<R><<<ctas, 256, 0, s>>>(x, n, p->red);
+    k_sum<<<1, 256, 0, s>>>(p->red, ctas, out);
+    return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_scale_copy(const R* __restrict__ x, R* __restrict__ y, int64_t n, R scale) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = x[i] * scale;
+}
+template <typename R>
+cudaError_t scale_copy(const R* x, R* y, int64_t n, double scale, cudaStream_t s) {
+    const int ctas = (int)std::min<int64_t>(4096, (n + 255) / 256);
+    k_scale_copy<R><<<ctas, 256, 0, s>>>(x, y, n, (R)scale);
+    return cudaGetLastError();
+}
+
+template <typename C>
+__global__ void k_gather(const C* __restrict__ user, C* __restrict__ internal, const int32_t* __restrict__ perm,
+                         int64_t m) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        internal[i] = user[perm[i]];
+}
+template <typename C>
+__global__ void k_scatter(const C* __restrict__ internal, C* __restrict__ user, const int32_t* __restrict__ perm,
+                          int64_t m) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        user[perm[i]] = internal[i];
+}
+template <typename R>
+cudaError_t gather_internal(const pd_plan* p, const cplx_t<R>* user, cplx_t<R>* internal, cudaStream_t s) {
+    const int ctas = (int)std::min<int64_t>(4096, (p->M + 255) / 256);
+    k_gather<<<ctas, 256, 0, s>>>(user, internal, p->perm, p->M);
+    return cudaGetLastError();
+}
+template <typename R>
+cudaError_t scatter_user(const pd_plan* p, const cplx_t<R>* internal, cplx_t<R>* user, cudaStream_t s) {
+    const int ctas = (int)std::min<int64_t>(4096, (p->M + 255) / 256);
+    k_scatter<<<ctas, 256, 0, s>>>(internal, user, p->perm, p->M);
+    return cudaGetLastError();
+}
+
+// ||y_i|| per block (= ||Phi_i x^(0) - y_i|| for x^(0) = 0): chunk partials, then
+// a fixed-order sum per block.
+template <typename R>
+__global__ void k_chunk_sq(const cplx_t<R>* __restrict__ y, const int32_t* __restrict__ cs,
+                           const int32_t* __restrict__ ce, int nchunk, double* __restrict__ part) {
+    __shared__ double sh[32];
+    for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+        double a = 0.0;
+        for (int m = cs[c] + threadIdx.x; m < ce[c]; m += blockDim.x) a += (double)y[m].x * y[m].x + (double)y[m].y * y[m].y;
+        a = block_sum(a, sh);
+        if (threadIdx.x == 0) part[2 * c + 1] = a;
+    }
+}
+__global__ void k_block_sqrt(const double* __restrict__ part, const int32_t* __restrict__ bcs, int d,
+                             double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    double a = 0.0;
+    for (int c = bcs[i]; c < bcs[i + 1]; ++c) a += part[2 * c + 1];
+    out[i] = sqrt(a);
+}
+cudaError_t init_res_norm(const pd_plan* p, pd_state* st, cudaStream_t s) {
+    const int ctas = (int)std::min<int64_t>(p->nchunk, (int64_t)p->num_sms * 8);
+    if (p->prec == PD_F64)
+        k_chunk_sq<double><<<ctas, 256, 0, s>>>((const double2*)st->y, p->chunk_start, p->chunk_end, (int)p->nchunk,
+                                                p->chunk_part);
+    else
+        k_chunk_sq<float><<<ctas, 256, 0, s>>>((const float2*)st->y, p->chunk_start, p->chunk_end, (int)p->nchunk,
+                                               p->chunk_part);
+    k_block_sqrt<<<(p->d + 127) / 128, 128, 0, s>>>(p->chunk_part, p->block_chunk_start, p->d, st->res_norm);
+    return cudaGetLastError();
+}
+
+template cudaError_t norm2<float>(const pd_plan*, const float*, int64_t, double*, cudaStream_t);
+template cudaError_t norm2<double>(const pd_plan*, const double*, int64_t, double*, cudaStream_t);
+template cudaError_t scale_copy<float>(const float*, float*, int64_t, double, cudaStream_t);
+template cudaError_t scale_copy<double>(const double*, double*, int64_t, double, cudaStream_t);
+template cudaError_t gather_internal<float>(const pd_plan*, const float2*, float2*, cudaStream_t);
+template cudaError_t gather_internal<double>(const pd_plan*, const double2*, double2*, cudaStream_t);
+template cudaError_t scatter_user<float>(const pd_plan*, const float2*, float2*, cudaStream_t);
+template cudaError_t scatter_user<double>(const pd_plan*, const double2*, double2*, cudaStream_t);
+
+}  // namespace pdgb

@@ -1,0 +1,205 @@
+// Internal plan/state layout of the PD-R CUDA library and the launcher interfaces
+// between the host API (api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "pd.h"
+
+namespace pdgb {
+
+constexpr int PW = 4;          // panel width (complex elements) of the column-panel grid layout
+constexpr int MAX_FILTER = 16; // longest Daubechies filter (db8)
+constexpr int MAX_BASES = 16;
+constexpr int CHUNK = 1024;    // visibilities per degridding work item
+
+// Device-side view of the plan, passed by value to kernels.
+struct Geo {
+    int nx, ny, Kx, Ky;
+    int J;
+    double beta;
+    int tile, logT, ntx, nty, ntiles;
+    int ext;        // T + J - 1: extended tile edge of the gridding accumulator
+    int halo_lo;    // J/2 - 1 cells before the tile
+    int halo_hi;    // J/2 cells after the tile
+    int ring;       // ring cells per tile
+};
+
+struct pd_plan_impl;
+
+// Element offset of grid cell (ky, kx) in the column-panel layout [Kx/PW][K][PW].
+__host__ __device__ __forceinline__ int64_t panel_off(int ky, int kx, int K) {
+    return ((int64_t)(kx >> 2) * K + ky) * PW + (kx & 3);
+}
+
+}  // namespace pdgb
+
+struct pd_plan {
+    int prec;                  // PD_F32 / PD_F64
+    size_t rsz, csz;           // sizeof real / complex
+    pdgb::Geo g;
+    int64_t M;
+    int d, b, L;
+    std::vector<int> basis_ids;
+    int n_wavelet;             // bases with id > 0
+    int64_t nseg, nchunk;
+    int num_sms;
+    int device;
+
+    // host copies of the static tables
+    std::vector<int32_t> h_chunk_block, h_block_chunk_start;
+    std::vector<int32_t> h_tile_seg_start, h_seg_block;
+
+    // device: visibilities in internal (tile, block) order
+    int32_t* cell = nullptr;       // (by << 16) | bx of floor(g), mod K
+    void* fx = nullptr;            // real [M]: fractional part of g_x
+    void* fy = nullptr;
+    int32_t* perm = nullptr;       // internal -> user index
+    int32_t* seg_start = nullptr;  // [nseg + 1]
+    int32_t* seg_block = nullptr;  // [nseg]
+    int32_t* tile_seg_start = nullptr;  // [ntiles + 1]
+    int32_t* chunk_start = nullptr;     // [nchunk] internal range, block-major order
+    int32_t* chunk_end = nullptr;
+    int32_t* chunk_block = nullptr;
+    int32_t* block_chunk_start = nullptr;  // [d + 1]
+    int32_t* all_chunks = nullptr;         // 0..nchunk-1 and its count
+    int32_t* all_tiles = nullptr;          // 0..ntiles-1
+    int32_t* counts_all = nullptr;         // {nchunk, ntiles}
+    int32_t* ones_block = nullptr;         // all blocks active
+    int32_t* ones_basis = nullptr;
+
+    // tables
+    void* cx = nullptr;            // real [nx] deapodisation
+    void* cy = nullptr;            // real [ny]
+    void* twx = nullptr;           // complex [Kx]: exp(-2 pi i k / Kx)
+    void* twy = nullptr;           // complex [Ky]
+    void* filt = nullptr;          // real [b][MAX_FILTER] low-pass filters (0 for Dirac)
+    int32_t* filt_len = nullptr;   // [b]
+    std::vector<double> h_filt;    // host copy
+    std::vector<int> h_filt_len;
+
+    // scratch
+    void* t1 = nullptr;            // complex [Kx/PW][ny][PW] row-pass intermediate
+    void* gridb = nullptr;         // complex [Kx/PW][Ky][PW] b~ = F Z x~
+    void* gridu = nullptr;         // complex grid for the plain adjoint
+    void* rbuf = nullptr;          // complex [M] residuals r = v + G b - y (internal order)
+    double* chunk_part = nullptr;  // [2 * nchunk]
+    double* blk_norm = nullptr;    // [2 * d]: ||r_i||^2, ||G_i b - y_i||^2
+    void* blk_scale = nullptr;     // real [d]: max(0, 1 - eps_i / ||r_i||)
+    void* ringbuf = nullptr;       // complex [ntiles][ring]
+    int32_t* tile_ones = nullptr;  // [ntiles] all ones (every tile active in plain gridding)
+    void* ll[2] = {nullptr, nullptr};  // real [b][ny/2][nx/2] wavelet approximation ping-pong
+    void* ds = nullptr;            // real [b][ny][nx] change of the sparsity duals
+    double* red = nullptr;         // reduction scratch
+    int red_len = 0;
+    size_t device_bytes = 0;
+    std::vector<void*> allocs;     // every device allocation of the plan
+};
+
+struct pd_state {
+    pd_plan* plan = nullptr;
+    void* x = nullptr;
+    void* xt = nullptr;
+    void* s = nullptr;             // [b][ny][nx]
+    void* st = nullptr;            // s~ = Psi s
+    void* v = nullptr;             // complex [M] internal order
+    void* u = nullptr;             // complex grid G^T v (panel layout)
+    void* y = nullptr;             // complex [M] internal order
+    double* eps = nullptr;         // [d]
+    double* res_norm = nullptr;    // [d]
+    double* p_block = nullptr;     // [d]
+    double* p_basis = nullptr;     // [b]
+    int32_t* block_active = nullptr;   // [d]
+    int32_t* basis_active = nullptr;   // [b]
+    int32_t* act_chunks = nullptr;     // [nchunk]
+    int32_t* act_tiles = nullptr;      // [ntiles]
+    int32_t* tile_active = nullptr;    // [ntiles]: tile holds a visibility of an active block
+    int32_t* counts = nullptr;         // {active chunks, active tiles}
+    int64_t* t = nullptr;              // iteration counter (device)
+    double* diag = nullptr;            // [2]: ||dx||^2, ||x||^2
+    double* prim_part = nullptr;       // [2 * ny / rows-per-CTA]
+    int32_t* status = nullptr;         // device status word
+    std::vector<void*> allocs;
+    size_t device_bytes = 0;
+    // CUDA graph of one iteration
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey;
+    cudaStream_t gstream = nullptr;
+};
+
+namespace pdgb {
+
+// ---- fft.cu
+template <typename R>
+cudaError_t fwd_fft(const pd_plan* p, const R* x, cplx_t<R>* grid, cudaStream_t s);
+struct PrimalArgs {
+    double tau, sigma, varsigma;
+    void* x;           // in/out
+    void* xt;          // out
+    const void* st;    // s~
+    double* part;      // per-CTA partial sums
+};
+// mode 0: write Re(Z^T F^H grid) to out; mode 1: primal update (Alg. 1 steps 17-18)
+template <typename R>
+cudaError_t inv_fft(const pd_plan* p, const cplx_t<R>* grid, R* out, const PrimalArgs* pa, cudaStream_t s);
+int inv_rows_ctas(const pd_plan* p);
+
+// ---- gridding.cu
+struct DualArgs {
+    const void* y;        // internal-order data (pd mode) or user-order input (plain mode)
+    void* v;              // dual (pd mode)
+    const int32_t* block_active;
+    const double* eps;
+    double* res_norm;     // updated for active blocks
+};
+// plain degrid: out (user order) = G grid
+template <typename R>
+cudaError_t degrid_plain(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out_user, cudaStream_t s);
+// pd degrid over the listed chunks: r = v + G b - y, chunk partial norms, then block scales
+template <typename R>
+cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs& a, const int32_t* chunks,
+                        const int32_t* counts, cudaStream_t s);
+// plain grid: U = G^T y_user (U overwritten)
+template <typename R>
+cudaError_t grid_plain(const pd_plan* p, const cplx_t<R>* y_user, cplx_t<R>* U, cudaStream_t s);
+// pd grid over the listed tiles: v <- scale * r, U += G^T (v_new - v_old)
+template <typename R>
+cudaError_t grid_dual(const pd_plan* p, const DualArgs& a, const int32_t* tiles, const int32_t* counts,
+                      const int32_t* tile_active, cplx_t<R>* U, cudaStream_t s);
+
+// ---- wavelet.cu
+// plain analysis: coeffs[b][ny][nx] = Psi^H x
+template <typename R>
+cudaError_t psi_adj_plain(const pd_plan* p, const R* x, R* coeffs, cudaStream_t s);
+// plain synthesis: x = Psi coeffs
+template <typename R>
+cudaError_t psi_plain(const pd_plan* p, const R* coeffs, R* x, cudaStream_t s);
+// pd: for active bases s <- clip(s + Psi_j^H x~ / sqrt(b), -alpha, alpha); s~ += Psi (s_new - s_old)
+template <typename R>
+cudaError_t sparsity_dual(const pd_plan* p, const R* xt, R* s, R* st, const int32_t* basis_active,
+                          double alpha, cudaStream_t s_);
+
+// ---- pd_kernels.cu
+struct SelectArgs {
+    uint64_t seed;
+    int adaptive;
+    double n, p_min, p_max;
+};
+cudaError_t select_active(const pd_plan* p, pd_state* st, const SelectArgs& a, cudaStream_t s);
+cudaError_t primal_finish(const pd_plan* p, pd_state* st, cudaStream_t s);
+template <typename R>
+cudaError_t norm2(const pd_plan* p, const R* x, int64_t n, double* out, cudaStream_t s);
+template <typename R>
+cudaError_t scale_copy(const R* x, R* y, int64_t n, double scale, cudaStream_t s);
+template <typename R>
+cudaError_t gather_internal(const pd_plan* p, const cplx_t<R>* user, cplx_t<R>* internal, cudaStream_t s);
+template <typename R>
+cudaError_t scatter_user(const pd_plan* p, const cplx_t<R>* internal, cplx_t<R>* user, cudaStream_t s);
+cudaError_t init_res_norm(const pd_plan* p, pd_state* st, cudaStream_t s);
+
+}  // namespace pdgb

@@ -1,0 +1,381 @@
+// Sparsity dictionary Psi = b^{-1/2} [Psi_1 ... Psi_b] (Sec. 3: a collection of b
+// bases, the Dirac basis and Daubechies wavelets db1..db8), and the sparsity dual
+// update of Algorithm 1 steps 13-14.
+//
+// Periodic separable filter banks: analysis a_k = sum_j h_j x_{(2k+j) mod m},
+// d_k = sum_j g_j x_{(2k+j) mod m}, g_j = (-1)^j h_{L-1-j}; rows then columns;
+// L levels in the packed layout (coarsest approximation top-left). Synthesis is
+// the transpose. Each CTA stages one input tile plus its filter halo in shared
+// memory, filters rows then columns there, and writes the four sub-bands.
+//
+// Step 13 is s <- s + w - S_alpha(s + w) = clip(s + w, -alpha, alpha) (Moreau,
+// eq. prox-L1), fused into the analysis epilogue; the change ds = s_new - s_old
+// is synthesised and added to s~ (step 14) so that inactive bases cost nothing.
+#include <algorithm>
+
+#include "common.cuh"
+#include "plan.hpp"
+
+namespace pdgb {
+
+constexpr int AT = 32;   // analysis output tile edge (per sub-band)
+constexpr int ST = 64;   // synthesis output tile edge
+constexpr int NT_W = 256;
+
+template <typename R> __device__ __forceinline__ R clip(R v, R a) { return v > a ? a : (v < -a ? -a : v); }
+
+// -------------------------------------------------------------------- analysis
+// One level for every basis in blockIdx.z. MODE 0: out = coefficient * scale.
+// MODE 1: s/ds update of step 13. The last level also treats the approximation band.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(NT_W) k_dwt_level(const R* __restrict__ x0, const R* __restrict__ ll_in,
+                                                    R* __restrict__ ll_out, R* __restrict__ out, R* __restrict__ ds,
+                                                    const R* __restrict__ filt, const int32_t* __restrict__ flen,
+                                                    const int32_t* __restrict__ active, int level, int L, int ny,
+                                                    int nx, R scale, R alpha) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int k = blockIdx.z;
+    const int lf = flen[k];
+    if (lf == 0) return;                               // Dirac basis: separate kernel
+    if (MODE == 1 && !active[k]) return;
+    const int my = ny >> level, mx = nx >> level;
+    const int hy = my >> 1, hx = mx >> 1;
+    const int ty = min(AT, hy), tx = min(AT, hx);
+    const int oy0 = blockIdx.y * ty, ox0 = blockIdx.x * tx;
+    if (oy0 >= hy || ox0 >= hx) return;
+    const int IH = 2 * ty + lf - 2, IW = 2 * tx + lf - 2;
+    R* in = reinterpret_cast<R*>(smraw);              // [IH][IW]
+    R* ra = in + IH * IW;                              // [IH][tx]
+    R* rd = ra + IH * tx;                              // [IH][tx]
+    __shared__ R h[MAX_FILTER], g[MAX_FILTER];
+    if (threadIdx.x < lf) {
+        h[threadIdx.x] = filt[k * MAX_FILTER + threadIdx.x];
+        const int j = threadIdx.x;
+        g[j] = ((j & 1) ? R(-1) : R(1)) * filt[k * MAX_FILTER + lf - 1 - j];
+    }
+    const R* src = level == 0 ? x0 : ll_in + (int64_t)k * (ny / 2) * (nx / 2);
+    for (int i = threadIdx.x; i < IH * IW; i += blockDim.x) {
+        const int r = i / IW, c = i - r * IW;
+        const int gy = (2 * oy0 + r) & (my - 1), gx = (2 * ox0 + c) & (mx - 1);
+        in[i] = src[(int64_t)gy * mx + gx];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < IH * tx; i += blockDim.x) {
+        const int r = i / tx, c = i - r * tx;
+        const R* row = in + r * IW + 2 * c;
+        R a = 0, d = 0;
+        for (int j = 0; j < lf; ++j) { a += h[j] * row[j]; d += g[j] * row[j]; }
+        ra[i] = a;
+        rd[i] = d;
+    }
+    __syncthreads();
+    const int64_t boff = (int64_t)k * ny * nx;
+    const bool last = level == L - 1;
+    for (int i = threadIdx.x; i < ty * tx; i += blockDim.x) {
+        const int r = i / tx, c = i - r * tx;
+        R ll = 0, hl = 0, lh = 0, hh = 0;
+        for (int j = 0; j < lf; ++j) {
+            const R va = ra[(2 * r + j) * tx + c], vd = rd[(2 * r + j) * tx + c];
+            ll += h[j] * va; lh += g[j] * va;
+            hl += h[j] * vd; hh += g[j] * vd;
+        }
+        const int oy = oy0 + r, ox = ox0 + c;
+        const int64_t p_hl = boff + (int64_t)oy * nx + hx + ox;
+        const int64_t p_lh = boff + (int64_t)(hy + oy) * nx + ox;
+        const int64_t p_hh = boff + (int64_t)(hy + oy) * nx + hx + ox;
+        const int64_t p_ll = boff + (int64_t)oy * nx + ox;
+        if (MODE == 0) {
+            out[p_hl] = hl * scale; out[p_lh] = lh * scale; out[p_hh] = hh * scale;
+            if (last) out[p_ll] = ll * scale;
+        } else {
+            R so, sn;
+            so = out[p_hl]; sn = clip(so + hl * scale, alpha); out[p_hl] = sn; ds[p_hl] = sn - so;
+            so = out[p_lh]; sn = clip(so + lh * scale, alpha); out[p_lh] = sn; ds[p_lh] = sn - so;
+            so = out[p_hh]; sn = clip(so + hh * scale, alpha); out[p_hh] = sn; ds[p_hh] = sn - so;
+            if (last) { so = out[p_ll]; sn = clip(so + ll * scale, alpha); out[p_ll] = sn; ds[p_ll] = sn - so; }
+        }
+        if (!last) ll_out[(int64_t)k * (ny / 2) * (nx / 2) + (int64_t)oy * hx + ox] = ll;
+    }
+}
+
+// Dirac basis (identity): MODE 0 copies x * scale, MODE 1 applies step 13 elementwise.
+template <typename R, int MODE>
+__global__ void k_dirac(const R* __restrict__ x, R* __restrict__ out, R* __restrict__ ds,
+                        const int32_t* __restrict__ flen, const int32_t* __restrict__ active, int b, int64_t n,
+                        R scale, R alpha) {
+    for (int k = 0; k < b; ++k) {
+        if (flen[k] != 0 || (MODE == 1 && !active[k])) continue;
+        R* o = out + (int64_t)k * n;
+        R* d = ds + (int64_t)k * n;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            if (MODE == 0) {
+                o[i] = x[i] * scale;
+            } else {
+                const R so = o[i], sn = clip(so + x[i] * scale, alpha);
+                o[i] = sn;
+                d[i] = sn - so;
+            }
+        }
+    }
+}
+
+// -------------------------------------------------------------------- synthesis
+// Reconstruct an (ty x tx) tile of the level-`level` region (size my x mx) of basis k
+// from its four sub-bands; the approximation band comes from ll_in (or from the
+// packed coefficients at the coarsest level). Result left in `res` (shared).
+template <typename R>
+__device__ void synth_tile(const R* __restrict__ coef, const R* __restrict__ ll_in, int k, int level, int L, int ny,
+                           int nx, int oy0, int ox0, int ty, int tx, const R* h, const R* g, int lf, R* sm, R* res) {
+    const int my = ny >> level, mx = nx >> level;
+    const int hy = my >> 1, hx = mx >> 1;
+    const int NKy = ty / 2 + lf / 2 - 1, NKx = tx / 2 + lf / 2 - 1;
+    const int kby = oy0 / 2 - lf / 2 + 1, kbx = ox0 / 2 - lf / 2 + 1;
+    R* LLs = sm;                      // [NKy][NKx] x4 sub-bands
+    R* HLs = LLs + NKy * NKx;
+    R* LHs = HLs + NKy * NKx;
+    R* HHs = LHs + NKy * NKx;
+    R* lo = HHs + NKy * NKx;          // [ty][NKx] columns synthesised, low-x half
+    R* hi = lo + ty * NKx;
+    const int64_t boff = (int64_t)k * ny * nx;
+    const bool coarsest = level == L - 1;
+    const R* llsrc = ll_in + (int64_t)k * (ny / 2) * (nx / 2);
+    for (int i = threadIdx.x; i < NKy * NKx; i += blockDim.x) {
+        const int r = i / NKx, c = i - r * NKx;
+        const int gy = (kby + r) & (hy - 1), gx = (kbx + c) & (hx - 1);
+        LLs[i] = coarsest ? coef[boff + (int64_t)gy * nx + gx] : llsrc[(int64_t)gy * hx + gx];
+        HLs[i] = coef[boff + (int64_t)gy * nx + hx + gx];
+        LHs[i] = coef[boff + (int64_t)(hy + gy) * nx + gx];
+        HHs[i] = coef[boff + (int64_t)(hy + gy) * nx + hx + gx];
+    }
+    __syncthreads();
+    const int off = lf / 2 - 1;
+    for (int i = threadIdx.x; i < ty * NKx; i += blockDim.x) {
+        const int r = i / NKx, c = i - r * NKx;
+        R l = 0, hh = 0;
+        for (int j = r & 1; j < lf; j += 2) {
+            const int kk = ((r - j) >> 1) + off;
+            l += h[j] * LLs[kk * NKx + c] + g[j] * LHs[kk * NKx + c];
+            hh += h[j] * HLs[kk * NKx + c] + g[j] * HHs[kk * NKx + c];
+        }
+        lo[i] = l;
+        hi[i] = hh;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ty * tx; i += blockDim.x) {
+        const int r = i / tx, c = i - r * tx;
+        R v = 0;
+        for (int j = c & 1; j < lf; j += 2) {
+            const int kk = ((c - j) >> 1) + off;
+            v += h[j] * lo[r * NKx + kk] + g[j] * hi[r * NKx + kk];
+        }
+        res[i] = v;
+    }
+    __syncthreads();
+}
+
+// Levels L-1 .. 1 of one basis per blockIdx.z: reconstruct the (ny>>level) x (nx>>level)
+// approximation of the next finer level into ll_out.
+template <typename R>
+__global__ void __launch_bounds__(NT_W) k_idwt_level(const R* __restrict__ coef, const R* __restrict__ ll_in,
+                                                     R* __restrict__ ll_out, const R* __restrict__ filt,
+                                                     const int32_t* __restrict__ flen,
+                                                     const int32_t* __restrict__ active, int level, int L, int ny,
+                                                     int nx) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ R h[MAX_FILTER], g[MAX_FILTER];
+    const int k = blockIdx.z;
+    const int lf = flen[k];
+    if (lf == 0) return;
+    if (active && !active[k]) return;
+    const int my = ny >> level, mx = nx >> level;
+    const int ty = min(ST, my), tx = min(ST, mx);
+    const int oy0 = blockIdx.y * ty, ox0 = blockIdx.x * tx;
+    if (oy0 >= my || ox0 >= mx) return;
+    if (threadIdx.x < lf) {
+        const int j = threadIdx.x;
+        h[j] = filt[k * MAX_FILTER + j];
+        g[j] = ((j & 1) ? R(-1) : R(1)) * filt[k * MAX_FILTER + lf - 1 - j];
+    }
+    __syncthreads();
+    R* sm = reinterpret_cast<R*>(smraw);
+    R* res = sm + 4 * (ty / 2 + MAX_FILTER / 2) * (tx / 2 + MAX_FILTER / 2) + 2 * ty * (tx / 2 + MAX_FILTER / 2);
+    synth_tile<R>(coef, ll_in, k, level, L, ny, nx, oy0, ox0, ty, tx, h, g, lf, sm, res);
+    R* dst = ll_out + (int64_t)k * (ny / 2) * (nx / 2);
+    for (int i = threadIdx.x; i < ty * tx; i += blockDim.x) {
+        const int r = i / tx, c = i - r * tx;
+        dst[(int64_t)(oy0 + r) * mx + ox0 + c] = res[i];
+    }
+}
+
+// Level 0 for all bases at once: acc = sum_k Psi_k coef_k over active bases (Dirac
+// included); MODE 0: out = acc * scale, MODE 1: out += acc * scale (s~ update).
+template <typename R, int MODE>
+__global__ void __launch_bounds__(NT_W) k_idwt_final(const R* __restrict__ coef, const R* __restrict__ ll_in,
+                                                     R* __restrict__ out, const R* __restrict__ filt,
+                                                     const int32_t* __restrict__ flen,
+                                                     const int32_t* __restrict__ active, int b, int L, int ny,
+                                                     int nx, R scale) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ R h[MAX_FILTER], g[MAX_FILTER];
+    constexpr int PER = ST * ST / NT_W;
+    const int ty = min(ST, ny), tx = min(ST, nx);
+    const int oy0 = blockIdx.y * ty, ox0 = blockIdx.x * tx;
+    R acc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) acc[q] = 0;
+    R* sm = reinterpret_cast<R*>(smraw);
+    R* res = sm + 4 * (ty / 2 + MAX_FILTER / 2) * (tx / 2 + MAX_FILTER / 2) + 2 * ty * (tx / 2 + MAX_FILTER / 2);
+    for (int k = 0; k < b; ++k) {
+        if (MODE == 1 && !active[k]) continue;
+        const int lf = flen[k];
+        if (lf == 0) {
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int i = threadIdx.x + q * NT_W;
+                if (i < ty * tx) {
+                    const int r = i / tx, c = i - r * tx;
+                    acc[q] += coef[(int64_t)k * ny * nx + (int64_t)(oy0 + r) * nx + ox0 + c];
+                }
+            }
+            continue;
+        }
+        __syncthreads();
+        if (threadIdx.x < lf) {
+            const int j = threadIdx.x;
+            h[j] = filt[k * MAX_FILTER + j];
+            g[j] = ((j & 1) ? R(-1) : R(1)) * filt[k * MAX_FILTER + lf - 1 - j];
+        }
+        __syncthreads();
+        synth_tile<R>(coef, ll_in, k, 0, L, ny, nx, oy0, ox0, ty, tx, h, g, lf, sm, res);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int i = threadIdx.x + q * NT_W;
+            if (i < ty * tx) acc[q] += res[i];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = threadIdx.x + q * NT_W;
+        if (i < ty * tx) {
+            const int r = i / tx, c = i - r * tx;
+            const int64_t o = (int64_t)(oy0 + r) * nx + ox0 + c;
+            if (MODE == 0) out[o] = acc[q] * scale;
+            else out[o] += acc[q] * scale;
+        }
+    }
+}
+
+// -------------------------------------------------------------------- launchers
+template <typename R> static size_t ana_smem(int ty, int tx) {
+    const int IH = 2 * ty + MAX_FILTER - 2, IW = 2 * tx + MAX_FILTER - 2;
+    return (size_t)(IH * IW + 2 * IH * tx) * sizeof(R);
+}
+template <typename R> static size_t syn_smem(int ty, int tx) {
+    const int NKy = ty / 2 + MAX_FILTER / 2, NKx = tx / 2 + MAX_FILTER / 2;
+    return (size_t)(4 * NKy * NKx + 2 * ty * NKx + ty * tx) * sizeof(R);
+}
+
+template <typename R> static cudaError_t wav_attrs() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    const int big = 200 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_dwt_level<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_dwt_level<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_idwt_level<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_idwt_final<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_idwt_final<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    done = true;
+    return cudaSuccess;
+}
+
+template <typename R>
+static cudaError_t analysis(const pd_plan* p, const R* x, R* out, R* ds, const int32_t* active, int mode, R alpha,
+                            cudaStream_t s) {
+    cudaError_t e = wav_attrs<R>();
+    if (e) return e;
+    const int ny = p->g.ny, nx = p->g.nx, b = p->b, L = p->L;
+    const R scale = R(1.0 / std::sqrt((double)b));
+    const int64_t n = (int64_t)ny * nx;
+    int dgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)p->num_sms * 4);
+    if (mode == 0)
+        k_dirac<R, 0><<<dgrid, 256, 0, s>>>(x, out, out, p->filt_len, active, b, n, scale, alpha);
+    else
+        k_dirac<R, 1><<<dgrid, 256, 0, s>>>(x, out, ds, p->filt_len, active, b, n, scale, alpha);
+    if ((e = cudaGetLastError())) return e;
+    if (p->n_wavelet == 0) return cudaSuccess;
+    for (int lev = 0; lev < L; ++lev) {
+        const int hy = (ny >> lev) / 2, hx = (nx >> lev) / 2;
+        const int ty = std::min(AT, hy), tx = std::min(AT, hx);
+        dim3 grid((hx + tx - 1) / tx, (hy + ty - 1) / ty, b);
+        const R* llin = (const R*)p->ll[(lev + 1) & 1];
+        R* llout = (R*)p->ll[lev & 1];
+        const size_t sm = ana_smem<R>(ty, tx);
+        if (mode == 0)
+            k_dwt_level<R, 0><<<grid, NT_W, sm, s>>>(x, llin, llout, out, nullptr, (const R*)p->filt, p->filt_len,
+                                                     active, lev, L, ny, nx, scale, alpha);
+        else
+            k_dwt_level<R, 1><<<grid, NT_W, sm, s>>>(x, llin, llout, out, ds, (const R*)p->filt, p->filt_len, active,
+                                                     lev, L, ny, nx, scale, alpha);
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename R>
+static cudaError_t synthesis(const pd_plan* p, const R* coef, R* out, const int32_t* active, int mode,
+                             cudaStream_t s) {
+    cudaError_t e = wav_attrs<R>();
+    if (e) return e;
+    const int ny = p->g.ny, nx = p->g.nx, b = p->b, L = p->L;
+    const R scale = R(1.0 / std::sqrt((double)b));
+    if (p->n_wavelet > 0) {
+        for (int lev = L - 1; lev >= 1; --lev) {
+            const int my = ny >> lev, mx = nx >> lev;
+            const int ty = std::min(ST, my), tx = std::min(ST, mx);
+            dim3 grid((mx + tx - 1) / tx, (my + ty - 1) / ty, b);
+            k_idwt_level<R><<<grid, NT_W, syn_smem<R>(ty, tx), s>>>(
+                coef, (const R*)p->ll[(lev + 1) & 1], (R*)p->ll[lev & 1], (const R*)p->filt, p->filt_len,
+                mode == 1 ? active : nullptr, lev, L, ny, nx);
+            if ((e = cudaGetLastError())) return e;
+        }
+    }
+    const int ty = std::min(ST, ny), tx = std::min(ST, nx);
+    dim3 grid((nx + tx - 1) / tx, (ny + ty - 1) / ty, 1);
+    if (mode == 0)
+        k_idwt_final<R, 0><<<grid, NT_W, syn_smem<R>(ty, tx), s>>>(coef, (const R*)p->ll[1], out, (const R*)p->filt,
+                                                                   p->filt_len, active, b, L, ny, nx, scale);
+    else
+        k_idwt_final<R, 1><<<grid, NT_W, syn_smem<R>(ty, tx), s>>>(coef, (const R*)p->ll[1], out, (const R*)p->filt,
+                                                                   p->filt_len, active, b, L, ny, nx, scale);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t psi_adj_plain(const pd_plan* p, const R* x, R* coeffs, cudaStream_t s) {
+    return analysis<R>(p, x, coeffs, nullptr, p->ones_basis, 0, R(0), s);
+}
+
+template <typename R>
+cudaError_t psi_plain(const pd_plan* p, const R* coeffs, R* x, cudaStream_t s) {
+    return synthesis<R>(p, coeffs, x, p->ones_basis, 0, s);
+}
+
+template <typename R>
+cudaError_t sparsity_dual(const pd_plan* p, const R* xt, R* s, R* st, const int32_t* basis_active, double alpha,
+                          cudaStream_t str) {
+    cudaError_t e = analysis<R>(p, xt, s, (R*)p->ds, basis_active, 1, (R)alpha, str);
+    if (e) return e;
+    return synthesis<R>(p, (const R*)p->ds, st, basis_active, 1, str);
+}
+
+template cudaError_t psi_adj_plain<float>(const pd_plan*, const float*, float*, cudaStream_t);
+template cudaError_t psi_adj_plain<double>(const pd_plan*, const double*, double*, cudaStream_t);
+template cudaError_t psi_plain<float>(const pd_plan*, const float*, float*, cudaStream_t);
+template cudaError_t psi_plain<double>(const pd_plan*, const double*, double*, cudaStream_t);
+template cudaError_t sparsity_dual<float>(const pd_plan*, const float*, float*, float*, const int32_t*, double,
+                                          cudaStream_t);
+template cudaError_t sparsity_dual<double>(const pd_plan*, const double*, double*, double*, const int32_t*, double,
+                                           cudaStream_t);
+
+}  // namespace pdgb

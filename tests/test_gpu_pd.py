@@ -1,0 +1,115 @@
+"""GPU parity of Algorithm 1 (pd_iterate) against the oracle's step-by-step PD-R run."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from gpu_util import TOL_IT32, TOL_IT64, make_problem, rel  # noqa: E402
+from oracle import pd as PD  # noqa: E402
+from oracle import philox as PH  # noqa: E402
+from paper_1610_08895_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__ as ge
+    ge.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _setup(prob, precision, tile=0):
+    from paper_1610_08895_gb300.api import Plan, State
+    g = prob.geom
+    plan = Plan(g.nx, g.ny, prob.uv, prob.block_of_vis, prob.nblocks, kernel_width=g.J,
+                basis_ids=prob.basis_ids, levels=prob.levels, precision=precision, tile=tile)
+    st = State(plan)
+    st.pd_state_set_data(torch.tensor(prob.y, dtype=plan.cplx_dtype, device="cuda"), prob.eps)
+    return plan, st
+
+
+def _steps(prob):
+    x0 = synth.start_vector(prob.geom.ny, prob.geom.nx, seed=9)
+    phi2, psi2 = PD.operator_norms(prob, x0, max_iter=500, tol=1e-8)
+    return dict(tau=0.49, sigma=1.0 / psi2, varsigma=1.0 / phi2, kappa=1e-3, psi_norm=float(np.sqrt(psi2)))
+
+
+def test_deterministic_pd_fp64_config1_shape():
+    # 64x64 image, 128x128 grid, M = 4096, 4 equal blocks, 4x4 kernel, Dirac + db1-db4, 3 levels, p = 1
+    prob, _ = make_problem(64, 4096, 4, 4, (0, 1, 2, 3, 4), 3)
+    kw = _steps(prob)
+    niter = 200
+    st_ref, _ = PD.pd_run(prob, niter, seed=0, p_block=[1.0] * 4, p_basis=[1.0] * 5, **kw)
+    plan, st = _setup(prob, "f64")
+    st.pd_iterate(niter, seed=0, p_block=[1.0] * 4, p_basis=[1.0] * 5, **kw)
+    x = st.x().cpu().numpy()
+    assert rel(x, st_ref.x) < TOL_IT64
+    assert rel(st.s().cpu().numpy(), st_ref.s) < TOL_IT64
+    assert rel(st.v().cpu().numpy(), st_ref.v) < TOL_IT64
+    rep = st.report()
+    assert rep["t"] == niter
+    assert rep["dx2"] >= 0 and rep["x2"] == pytest.approx(np.sum(st_ref.x ** 2), rel=1e-9)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_randomised_pd_fp32_config2_shape(use_graph):
+    # 256x256, 512x512 grid, M = 65536, 16 blocks p = 0.5, 9 bases p = 0.5, 4 levels, 8x8 kernel
+    prob, _ = make_problem(256, 65536, 16, 8, tuple(range(9)), 4)
+    kw = _steps(prob)
+    niter = 40
+    pb, ps = [0.5] * 16, [0.5] * 9
+    st_ref, draws = PD.pd_run(prob, niter, seed=0, p_block=pb, p_basis=ps, **kw)
+    plan, st = _setup(prob, "f32")
+    st.pd_iterate(niter, seed=0, p_block=pb, p_basis=ps, use_graph=use_graph, **kw)
+    rep = st.report()
+    assert list(rep["block_active"]) == list(draws[-1][0])      # same seeded draws
+    assert list(rep["basis_active"]) == list(draws[-1][1])
+    assert rel(st.x().cpu().numpy(), st_ref.x) < TOL_IT32
+    assert rel(st.v().cpu().numpy(), st_ref.v) < TOL_IT32
+
+
+def test_adaptive_probabilities_uneven_blocks():
+    # radially decaying coverage split in annuli (uneven blocks), probabilities by eq. prob-choice
+    prob, _ = make_problem(64, 16384, 16, 8, (0, 1, 2), 2, uv_kind="radial", blocks="annuli", nannuli=16)
+    kw = _steps(prob)
+    ad = {"n": 4.0, "p_min": 0.05, "p_max": 0.5}
+    niter = 30
+    st_ref, draws = PD.pd_run(prob, niter, seed=3, p_block=None, p_basis=[1.0] * 3, adaptive=ad, **kw)
+    plan, st = _setup(prob, "f32")
+    st.pd_iterate(niter, seed=3, p_basis=[1.0] * 3, adaptive=ad, **kw)
+    rep = st.report()
+    assert list(rep["block_active"]) == list(draws[-1][0])
+    assert rel(st.x().cpu().numpy(), st_ref.x) < TOL_IT32
+    assert np.allclose(rep["res_norm"], st_ref.res_norm, rtol=1e-4)
+    assert rep["p_block"].sum() == pytest.approx(4.0, rel=1e-9)
+
+
+def test_checkpoint_resume_matches_uninterrupted_run():
+    prob, _ = make_problem(64, 8192, 4, 8, (0, 1, 2), 2)
+    kw = _steps(prob)
+    args = dict(seed=7, p_block=[0.5] * 4, p_basis=[0.5] * 3, **kw)
+    plan, st = _setup(prob, "f64")
+    st.pd_iterate(10, **args)
+    buf = st.save()
+    st.pd_iterate(10, **args)
+    x_full = st.x().cpu().numpy()
+    from paper_1610_08895_gb300.api import State
+    st2 = State(plan)
+    st2.load(buf)
+    st2.pd_iterate(10, **args)
+    assert st2.report()["t"] == 20
+    assert rel(st2.x().cpu().numpy(), x_full) < 1e-12
+
+
+def test_draws_match_oracle_philox_every_iteration():
+    prob, _ = make_problem(32, 2000, 9, 4, (0, 1), 1)
+    kw = _steps(prob)
+    plan, st = _setup(prob, "f32")
+    pb = [0.3] * 9
+    ps = [0.6, 0.6]
+    for t in range(1, 16):
+        st.pd_iterate(1, seed=11, p_block=pb, p_basis=ps, **kw)
+        rep = st.report()
+        assert list(rep["block_active"]) == PH.active_set(11, t, 0, pb)
+        assert list(rep["basis_active"]) == PH.active_set(11, t, 1, ps)
