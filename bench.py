@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Throughput of one randomised primal-dual (PD-R) iteration on GB300.
+
+Workload (default "c5"): 2048x2048 image, 4096x4096 complex64 grid,
+M = 16,777,216 visibilities with radially decaying density (inner 8x denser),
+256 uneven blocks (32 annuli x 8 sectors), 8x8 Kaiser-Bessel kernel evaluated
+on the fly, Dirac + db1..db8 at 4 levels, every block and basis drawn with
+p = 0.5, 30 dB noise. One step = one full iteration of Algorithm 1 (draws,
+F Z x~, degridding + l2-ball duals, gridding, wavelet duals, F^H + primal).
+
+Prints one JSON line. Multi-GPU runs (torchrun) solve one independent problem
+per rank (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c5": dict(n=2048, m=16_777_216, nannuli=32, nsectors=8, J=8, bases=list(range(9)), levels=4, p=0.5,
+               snr=30.0),
+    # the reference arm and the CPU baseline run the oracle on this 16x smaller version of c5
+    "c5_div16": dict(n=512, m=1_048_576, nannuli=32, nsectors=8, J=8, bases=list(range(9)), levels=4, p=0.5,
+                     snr=30.0),
+    "small": dict(n=256, m=65_536, nannuli=4, nsectors=4, J=8, bases=list(range(9)), levels=4, p=0.5, snr=30.0),
+}
+METRIC = "PD iters/s @2048^2 img, 16.8M vis (FP32 batched graph)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def make_inputs(cfg, seed):
+    from paper_1610_08895_gb300 import synth
+    uv = synth.uv_radial(cfg["m"], seed=seed + 1)
+    blk = synth.blocks_annuli(uv, cfg["nannuli"], cfg["nsectors"])
+    x_true = synth.test_image(cfg["n"], seed=seed + 2)
+    noise = synth.complex_noise(cfg["m"], seed=seed + 3)
+    return uv, blk, x_true, noise
+
+
+def epsilon(sigma_n, sizes):
+    from scipy.stats import chi2
+    m = np.maximum(np.asarray(sizes, dtype=np.float64), 1.0)
+    return sigma_n / np.sqrt(2.0) * np.sqrt(chi2.ppf(0.99, 2.0 * m))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler (its own child process, 50 ms period) of SM clocks and throttle
+    reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            cols = [c.strip() for c in line.split(",")]
+            if len(cols) >= 8:
+                self.samples.append(cols)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(s[1]) for s in self.samples if num(s[1]) is not None]
+        mx = [num(s[2]) for s in self.samples if num(s[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[4 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def algorithmic_bytes(cfg, plan_info, m_active, tiles_active_frac, bases_active, dirac_active):
+    """Bytes each phase must move per launch (FP32): the reads and writes its result needs."""
+    n = cfg["n"]
+    N = n * n
+    K = 4 * N
+    L = cfg["levels"]
+    ll = sum(8.0 * N / 4 ** l for l in range(1, L))          # one write + one read of the approximations
+    wav = bases_active - dirac_active
+    return {
+        "fwd_rows": 4 * N + 16 * N,
+        "fwd_cols": 16 * N + 32 * N,
+        "degrid_dual": 36 * m_active + 8 * K * tiles_active_frac,
+        "grid_dual": 36 * m_active + 16 * K * tiles_active_frac,
+        "wavelet_analysis": 4 * N + wav * (12 * N + ll) + dirac_active * 12 * N,
+        "wavelet_synthesis": wav * (4 * N + ll) + dirac_active * 4 * N + 8 * N,
+        "inv_cols": 32 * N + 16 * N,
+        "inv_rows_primal": 16 * N + 16 * N,
+    }
+
+
+KERNELS_PER_ITER = lambda L: 1 + 2 + 2 + 2 + (1 + L) + (L - 1 + 1) + 2 + 1   # noqa: E731
+
+
+# ---------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1610_08895_gb300.api import Plan, State
+
+    cfg = WORKLOADS[args.workload]
+    n, m = cfg["n"], cfg["m"]
+    t0 = time.time()
+    uv, blk, x_true, noise = make_inputs(cfg, args.seed + 100 * rank)
+    d = int(blk.max()) + 1
+    b = len(cfg["bases"])
+    plan = Plan(n, n, uv, blk, d, kernel_width=cfg["J"], basis_ids=cfg["bases"], levels=cfg["levels"],
+                precision="f32")
+    info = plan.info()
+    sizes = np.bincount(blk, minlength=d)
+    # measurements y = Phi x + n (Phi on the GPU), bounds from the chi-square quantile
+    xt = torch.tensor(x_true, dtype=torch.float32, device="cuda")
+    phix = plan.pd_apply_phi(xt)
+    sig = float(torch.linalg.vector_norm(phix.to(torch.complex128)).item()) / np.sqrt(m) * 10 ** (-cfg["snr"] / 20)
+    y_host = (phix.cpu().numpy().astype(np.complex128) + sig * noise).astype(np.complex64)
+    y = torch.tensor(y_host, device="cuda")
+    eps = epsilon(sig, sizes)
+    x0 = torch.tensor(np.random.default_rng(9).normal(size=(n, n)), dtype=torch.float32, device="cuda")
+    phi2, psi2, _ = plan.pd_operator_norms(x0, max_iter=20, tol=1e-3)
+    kw = dict(tau=0.49, sigma=1.0 / psi2, varsigma=1.0 / phi2, kappa=1e-3, psi_norm=float(np.sqrt(psi2)),
+              seed=args.seed, p_block=[cfg["p"]] * d, p_basis=[cfg["p"]] * b)
+    st = State(plan)
+    st.pd_state_set_data(y, eps)
+    setup_s = time.time() - t0
+
+    # ---- warm-up, then the timed region: K graph replays of one iteration
+    st.pd_iterate(args.warmup, use_graph=True, **kw)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        st.pd_iterate(args.steps, use_graph=True, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * args.steps / (ms / 1e3)
+
+    # ---- per-kernel times (CUDA events on the launching stream) over K instrumented iterations
+    st.profile(reset=True)
+    m_act, t_act, nb_act, dirac_act = 0.0, 0.0, 0.0, 0.0
+    dirac_slots = [k for k, bid in enumerate(cfg["bases"]) if bid == 0]
+    for _ in range(args.steps):
+        st.pd_iterate(1, profile=True, **kw)
+        rep = st.report()
+        m_act += float(sizes[rep["block_active"]].sum())
+        t_act += rep["active_tiles"] / info["kx"] / info["ky"] * info["tile"] ** 2
+        nb_act += float(rep["basis_active"].sum())
+        dirac_act += float(sum(rep["basis_active"][k] for k in dirac_slots))
+    prof = st.profile()
+    k_steps = float(args.steps)
+    alg = algorithmic_bytes(cfg, info, m_act / k_steps, t_act / k_steps, nb_act / k_steps, dirac_act / k_steps)
+    kernels = {}
+    for name, (tot_ms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        avg = tot_ms / cnt
+        entry = {"ms": round(avg, 4)}
+        if name in alg:
+            entry["GBps"] = round(alg[name] / (avg / 1e3) / 1e9, 1)
+        kernels[name] = entry
+    dom = max((k for k in kernels if k in alg), key=lambda k: kernels[k]["ms"])
+    peak, peak_kind = peaks()
+    achieved = kernels[dom]["GBps"]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": None, "algorithmic_bytes_per_launch": int(alg[dom])}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        y_pin = torch.from_numpy(y_host).pin_memory()
+        x_pin = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        y_dev = torch.empty(m, dtype=torch.complex64, device="cuda")
+        st2 = State(plan)
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        y_dev.copy_(y_pin, non_blocking=True)
+        st2.pd_state_set_data(y_dev, eps)
+        d2h = 0
+        for _ in range(args.steps):
+            st2.pd_iterate(1, **kw)
+            st2.report()                      # per-step result to host: t, ||dx||^2, ||x||^2 (+ block data)
+            d2h += 8 + 16 + d * (8 + 8 + 4) + b * 4
+        x_pin.copy_(st2.x(), non_blocking=True)
+        torch.cuda.synchronize()
+        t_b = time.perf_counter()
+        d2h += n * n * 4
+        h2d = m * 8 + args.steps * (d + b) * 8
+        e2e = {"value": round(args.steps / (t_b - t_a), 3), "unit": "PD iters/s",
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
+        st2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.seed, steps=2, warmup=1)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "PD iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "gpu_launches": KERNELS_PER_ITER(cfg["levels"]) * args.steps,
+            "config": {"workload": f"{args.workload}: {n}x{n} image, {2 * n}x{2 * n} grid, M={m}, "
+                                   f"{d} uneven blocks (annuli x sectors), J={cfg['J']} KB on the fly, "
+                                   f"{b} bases x {cfg['levels']} levels, p_block=p_basis={cfg['p']}",
+                       "global_batch": world, "parallelism": f"replicas x{world} (independent problems)",
+                       "l2": "working set > L2 (grid 134 MB + visibilities 600 MB per iteration)",
+                       "graph": "one CUDA graph per iteration, replayed", "setup_s": round(setup_s, 1),
+                       "plan": info},
+            "roofline": roofline, "kernels": kernels, "clocks": clk.summary(), "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------------
+def oracle_problem(cfg, seed):
+    """The oracle's problem on a workload (used only by the CPU legs)."""
+    from oracle import experiment as EX
+    from oracle import measurement as meas
+    from oracle import pd as PD
+    uv, blk, x_true, noise = make_inputs(cfg, seed)
+    d = int(blk.max()) + 1
+    prob = PD.Problem(meas.Geometry(cfg["n"], cfg["n"], cfg["J"]), uv, blk, d, cfg["bases"], cfg["levels"])
+    phix = prob.phi(x_true)
+    sn = EX.noise_sigma(phix, cfg["snr"])
+    prob.y = phix + sn * noise
+    prob.eps = EX.epsilon_bounds(sn, [max(len(ix), 1) for ix in prob.block_index])
+    return prob
+
+
+def cpu_baseline(seed, steps, warmup):
+    """Oracle iterations/s, timed on this host: the c5 workload shrunk 16x in pixels and
+    visibilities (512^2 image, 1,048,576 visibilities, same blocks, bases and levels), then
+    divided by 16 to express it per full c5 iteration (its cost is linear in both, up to the
+    FFT's log factor, so this overstates the oracle's full-size speed slightly)."""
+    from oracle import pd as PD
+    cfg = WORKLOADS["c5_div16"]
+    prob = oracle_problem(cfg, seed)
+    d, b = prob.nblocks, len(prob.basis_ids)
+    kw = dict(tau=0.49, sigma=1.0, varsigma=1e-6, kappa=1e-3, psi_norm=1.0, seed=seed,
+              p_block=[cfg["p"]] * d, p_basis=[cfg["p"]] * b)
+    st = PD.PDState(prob)
+    for _ in range(warmup):
+        PD.pd_iteration(prob, st, **kw)
+    t = time.perf_counter()
+    for _ in range(steps):
+        PD.pd_iteration(prob, st, **kw)
+    dt = (time.perf_counter() - t) / steps
+    return {"value": round(1.0 / dt / 16.0, 6), "unit": "PD iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle iterations (after {warmup} warm-up) of the c5 workload shrunk 16x "
+                      f"(512^2 image, 1,048,576 visibilities, 256 blocks, 9 bases, 4 levels), "
+                      f"{dt:.2f} s each, scaled by 1/16 to one c5 iteration; numpy single-threaded"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import pd as PD
+    cfg = WORKLOADS["c5_div16"]
+    prob = oracle_problem(cfg, args.seed)
+    d, b = prob.nblocks, len(prob.basis_ids)
+    kw = dict(tau=0.49, sigma=1.0, varsigma=1e-6, kappa=1e-3, psi_norm=1.0, seed=args.seed,
+              p_block=[cfg["p"]] * d, p_basis=[cfg["p"]] * b)
+    st = PD.PDState(prob)
+    for _ in range(args.warmup):
+        PD.pd_iteration(prob, st, **kw)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        PD.pd_iteration(prob, st, **kw)
+    dt = time.perf_counter() - t
+    value = args.steps / dt / 16.0
+    sample = (f"each step: one oracle iteration of the c5 workload shrunk 16x (512^2 image, "
+              f"1,048,576 visibilities, 256 blocks, 9 bases, 4 levels), {dt / args.steps:.2f} s, "
+              f"scaled by 1/16 to one c5 iteration; numpy single-threaded")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "PD iters/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3 * 16.0, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "c5 (oracle on the 16x smaller c5_div16 sample)"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "PD iters/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": "PD iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -181,6 +181,8 @@ typedef struct {
     int32_t adaptive;              /* 1: p_block from Sec. 4 eq. prob-choice */
     double adapt_n, adapt_p_min, adapt_p_max;   /* n, p_check, p_hat of eq. prob-choice */
     int32_t use_graph;             /* 1: capture one iteration in a CUDA graph and replay it */
+    int32_t profile;               /* 1 (and use_graph = 0): time every kernel phase with CUDA
+                                      events on `stream`; synchronises after each iteration */
 } pd_params;
 
 /*
@@ -196,6 +198,15 @@ typedef struct {
 pd_status pd_iterate(pd_plan* plan, pd_state* st, const pd_params* params, int32_t niter,
                      void* stream);
 
+/*
+ * Per-phase kernel times accumulated by iterations run with params.profile = 1:
+ * ms[k] (host) is the summed CUDA-event time of phase k and iterations[k] how
+ * many iterations contributed, for k < min(n, 12); reset = 1 clears the sums.
+ * Phase names come from pd_phase_name(k) (e.g. "degrid_dual", "fwd_cols").
+ */
+pd_status pd_state_profile(pd_state* st, double* ms, int64_t* iterations, int32_t n, int32_t reset);
+const char* pd_phase_name(int32_t phase);
+
 /* Copies out of the state (device destinations; asynchronous). */
 pd_status pd_state_get_x(const pd_state* st, void* x, void* stream);
 pd_status pd_state_get_x_tilde(const pd_state* st, void* x_tilde, void* stream);
@@ -208,11 +219,13 @@ pd_status pd_state_get_v(const pd_plan* plan, const pd_state* st, void* v, void*
  * ||G_i b~ - y_i|| of the last iteration each block was active (host
  * [nblocks], may be NULL), current block probabilities (host [nblocks], may be
  * NULL) and the activity of the last draw (host int32 [nblocks] and
- * [nbases], may be NULL).
+ * [nbases], may be NULL), and the size of the last iteration's work lists (host
+ * int32 [2]: degridding chunks of active blocks, tiles holding an active block;
+ * may be NULL).
  */
 pd_status pd_state_report(const pd_plan* plan, const pd_state* st, int64_t* t, double* dx2,
                           double* x2, double* res_norm, double* p_block, int32_t* block_active,
-                          int32_t* basis_active, void* stream);
+                          int32_t* basis_active, int32_t* work, void* stream);
 
 /*
  * Checkpoint: the full state as one host byte buffer. pd_state_save writes

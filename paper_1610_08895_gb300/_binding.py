@@ -39,7 +39,7 @@ class PdParams(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("psi_norm", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("p_block", ctypes.c_void_p), ("p_basis", ctypes.c_void_p), ("adaptive", ctypes.c_int32),
                 ("adapt_n", ctypes.c_double), ("adapt_p_min", ctypes.c_double),
-                ("adapt_p_max", ctypes.c_double), ("use_graph", ctypes.c_int32)]
+                ("adapt_p_max", ctypes.c_double), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32)]
 
 
 _lib = None
@@ -63,8 +63,10 @@ _SIGS = {
     "pd_state_get_x_tilde": ([_VP, _VP, _VP], ctypes.c_int),
     "pd_state_get_s": ([_VP, _VP, _VP], ctypes.c_int),
     "pd_state_get_v": ([_VP, _VP, _VP, _VP], ctypes.c_int),
-    "pd_state_report": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "pd_state_report": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "pd_state_bytes": ([_VP], ctypes.c_size_t),
+    "pd_state_profile": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "pd_phase_name": ([ctypes.c_int32], ctypes.c_char_p),
     "pd_state_save": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "pd_state_load": ([_VP, _VP, _VP, _VP], ctypes.c_int),
 }

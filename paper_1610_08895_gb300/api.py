@@ -163,13 +163,14 @@ class State:
         B.call("pd_state_set_data", p.handle, self._h, _ptr(y), eps.ctypes.data, _stream())
 
     def pd_iterate(self, niter, tau, sigma, varsigma, kappa, psi_norm=1.0, seed=0, p_block=None, p_basis=None,
-                   adaptive=None, use_graph=False):
+                   adaptive=None, use_graph=False, profile=False):
         p = self.plan
         pb = np.ascontiguousarray(np.ones(p.nblocks) if p_block is None else p_block, dtype=np.float64)
         ps = np.ascontiguousarray(np.ones(p.nbases) if p_basis is None else p_basis, dtype=np.float64)
         prm = B.PdParams(tau=tau, sigma=sigma, varsigma=varsigma, kappa=kappa, psi_norm=psi_norm, seed=int(seed),
                          p_block=pb.ctypes.data, p_basis=ps.ctypes.data, adaptive=0, adapt_n=0.0,
-                         adapt_p_min=0.0, adapt_p_max=0.0, use_graph=int(bool(use_graph)))
+                         adapt_p_min=0.0, adapt_p_max=0.0, use_graph=int(bool(use_graph)),
+                         profile=int(bool(profile)))
         if adaptive is not None:
             prm.adaptive = 1
             prm.adapt_n = float(adaptive["n"])
@@ -208,10 +209,20 @@ class State:
         pb = np.zeros(p.nblocks)
         ba = np.zeros(p.nblocks, dtype=np.int32)
         sa = np.zeros(p.nbases, dtype=np.int32)
+        work = np.zeros(2, dtype=np.int32)
         B.call("pd_state_report", p.handle, self._h, ctypes.byref(t), ctypes.byref(dx2), ctypes.byref(x2),
-               res.ctypes.data, pb.ctypes.data, ba.ctypes.data, sa.ctypes.data, _stream())
+               res.ctypes.data, pb.ctypes.data, ba.ctypes.data, sa.ctypes.data, work.ctypes.data, _stream())
         return {"t": t.value, "dx2": dx2.value, "x2": x2.value, "res_norm": res, "p_block": pb,
-                "block_active": ba.astype(bool), "basis_active": sa.astype(bool)}
+                "block_active": ba.astype(bool), "basis_active": sa.astype(bool),
+                "active_chunks": int(work[0]), "active_tiles": int(work[1])}
+
+    def profile(self, reset=False):
+        """{phase name: (total ms, iterations)} from iterations run with profile=True."""
+        ms = np.zeros(12)
+        n = np.zeros(12, dtype=np.int64)
+        B.call("pd_state_profile", self._h, ms.ctypes.data, n.ctypes.data, 12, int(bool(reset)))
+        lib = B.load()
+        return {lib.pd_phase_name(k).decode(): (float(ms[k]), int(n[k])) for k in range(12)}
 
     def save(self):
         p = self.plan

@@ -28,6 +28,22 @@ static pd_status fail(pd_status s, const std::string& msg) {
 
 extern "C" const char* pd_last_error(void) { return g_err.c_str(); }
 
+// ---- per-phase CUDA-event timing (pd_params.profile)
+static thread_local pd_state* g_prof = nullptr;
+
+void pdgb::prof_mark(int phase, int end, cudaStream_t s) {
+    if (!g_prof || phase < 0 || phase >= PH_COUNT) return;
+    cudaEventRecord(g_prof->prof_ev[2 * phase + end], s);
+}
+
+static const char* k_phase_names[PH_COUNT] = {
+    "select", "fwd_rows", "fwd_cols", "degrid_dual", "block_norms", "grid_dual", "halo_merge",
+    "wavelet_analysis", "wavelet_synthesis", "inv_cols", "inv_rows_primal", "primal_finish"};
+
+extern "C" const char* pd_phase_name(int32_t phase) {
+    return phase >= 0 && phase < PH_COUNT ? k_phase_names[phase] : "unknown";
+}
+
 static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 static int ilog2(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
 
@@ -467,6 +483,11 @@ extern "C" pd_status pd_operator_norms(pd_plan* p, const void* x0, int32_t max_i
 extern "C" pd_status pd_state_destroy(pd_state* st) {
     if (!st) return PD_OK;
     if (st->gexec) cudaGraphExecDestroy(st->gexec);
+    if (st->ev_in) cudaEventDestroy(st->ev_in);
+    if (st->ev_out) cudaEventDestroy(st->ev_out);
+    if (st->gstream) cudaStreamDestroy(st->gstream);
+    for (cudaEvent_t e : st->prof_ev)
+        if (e) cudaEventDestroy(e);
     free_all(st->allocs);
     delete st;
     return PD_OK;
@@ -581,18 +602,26 @@ extern "C" pd_status pd_iterate(pd_plan* p, pd_state* st, const pd_params* prm, 
     if (!prm->adaptive) CU(cudaMemcpyAsync(st->p_block, prm->p_block, p->d * sizeof(double), cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(st->p_basis, prm->p_basis, p->b * sizeof(double), cudaMemcpyHostToDevice, s));
     if (niter == 0) return PD_OK;
-    auto enqueue = [&]() {
-        return p->prec == PD_F64 ? enqueue_iteration<double>(p, st, prm, s) : enqueue_iteration<float>(p, st, prm, s);
-    };
     if (prm->use_graph) {
-        std::vector<unsigned char> key = params_key(p, prm, s);
+        // The caller's stream may be the legacy default stream, which cannot be captured:
+        // capture and replay on the state's private stream, fenced by events both ways.
+        if (!st->gstream) {
+            CU(cudaStreamCreateWithFlags(&st->gstream, cudaStreamNonBlocking));
+            CU(cudaEventCreateWithFlags(&st->ev_in, cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&st->ev_out, cudaEventDisableTiming));
+        }
+        cudaStream_t gs = st->gstream;
+        CU(cudaEventRecord(st->ev_in, s));
+        CU(cudaStreamWaitEvent(gs, st->ev_in, 0));
+        std::vector<unsigned char> key = params_key(p, prm, gs);
         if (!st->gexec || key != st->gkey) {
             if (st->gexec) { cudaGraphExecDestroy(st->gexec); st->gexec = nullptr; }
             // relaxed mode: kernel attribute calls made while enqueueing are allowed
-            CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-            cudaError_t e = enqueue();
+            CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed));
+            cudaError_t e = p->prec == PD_F64 ? enqueue_iteration<double>(p, st, prm, gs)
+                                              : enqueue_iteration<float>(p, st, prm, gs);
             cudaGraph_t graph = nullptr;
-            cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+            cudaError_t e2 = cudaStreamEndCapture(gs, &graph);
             if (e) { if (graph) cudaGraphDestroy(graph); return fail(PD_ECUDA, std::string("capture: ") + cudaGetErrorString(e)); }
             CU(e2);
             cudaError_t e3 = cudaGraphInstantiate(&st->gexec, graph, 0);
@@ -600,10 +629,44 @@ extern "C" pd_status pd_iterate(pd_plan* p, pd_state* st, const pd_params* prm, 
             CU(e3);
             st->gkey = key;
         }
-        for (int k = 0; k < niter; ++k) CU(cudaGraphLaunch(st->gexec, s));
+        for (int k = 0; k < niter; ++k) CU(cudaGraphLaunch(st->gexec, gs));
+        CU(cudaEventRecord(st->ev_out, gs));
+        CU(cudaStreamWaitEvent(s, st->ev_out, 0));
+    } else if (prm->profile) {
+        if (!st->prof_ev[0])
+            for (cudaEvent_t& e : st->prof_ev) CU(cudaEventCreate(&e));
+        for (int k = 0; k < niter; ++k) {
+            for (cudaEvent_t e : st->prof_ev) CU(cudaEventRecord(e, s));   // phases not run read 0 ms
+            g_prof = st;
+            cudaError_t e = p->prec == PD_F64 ? enqueue_iteration<double>(p, st, prm, s)
+                                              : enqueue_iteration<float>(p, st, prm, s);
+            g_prof = nullptr;
+            CU(e);
+            CU(cudaStreamSynchronize(s));
+            for (int ph = 0; ph < PH_COUNT; ++ph) {
+                float ms = 0.f;
+                CU(cudaEventElapsedTime(&ms, st->prof_ev[2 * ph], st->prof_ev[2 * ph + 1]));
+                st->prof_ms[ph] += ms;
+                st->prof_n[ph] += 1;
+            }
+        }
     } else {
-        for (int k = 0; k < niter; ++k) CU(enqueue());
+        for (int k = 0; k < niter; ++k) {
+            if (p->prec == PD_F64) CU(enqueue_iteration<double>(p, st, prm, s));
+            else CU(enqueue_iteration<float>(p, st, prm, s));
+        }
     }
+    return PD_OK;
+}
+
+extern "C" pd_status pd_state_profile(pd_state* st, double* ms, int64_t* iterations, int32_t n, int32_t reset) {
+    if (!st || n < 0) return fail(PD_EINVAL, "pd_state_profile: bad argument");
+    for (int ph = 0; ph < PH_COUNT && ph < n; ++ph) {
+        if (ms) ms[ph] = st->prof_ms[ph];
+        if (iterations) iterations[ph] = st->prof_n[ph];
+    }
+    if (reset)
+        for (int ph = 0; ph < PH_COUNT; ++ph) { st->prof_ms[ph] = 0.0; st->prof_n[ph] = 0; }
     return PD_OK;
 }
 
@@ -635,7 +698,7 @@ extern "C" pd_status pd_state_get_v(const pd_plan* p, const pd_state* st, void* 
 
 extern "C" pd_status pd_state_report(const pd_plan* p, const pd_state* st, int64_t* t, double* dx2, double* x2,
                                      double* res_norm, double* p_block, int32_t* block_active, int32_t* basis_active,
-                                     void* stream) {
+                                     int32_t* work, void* stream) {
     if (!p || !st || st->plan != p) return fail(PD_EINVAL, "pd_state_report: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t th = 0;
@@ -646,6 +709,7 @@ extern "C" pd_status pd_state_report(const pd_plan* p, const pd_state* st, int64
     if (p_block) CU(cudaMemcpyAsync(p_block, st->p_block, p->d * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (block_active) CU(cudaMemcpyAsync(block_active, st->block_active, p->d * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     if (basis_active) CU(cudaMemcpyAsync(basis_active, st->basis_active, p->b * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (work) CU(cudaMemcpyAsync(work, st->counts, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (t) *t = th;
     if (dx2) *dx2 = dg[0];

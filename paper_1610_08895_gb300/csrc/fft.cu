@@ -298,44 +298,40 @@ int inv_rows_ctas(const pd_plan* p) {
     return p->g.ny / c.rows_per_cta;
 }
 
-template <typename R> static cudaError_t set_smem_attrs() {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    const int big = 227 * 1024;
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_fwd_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_fwd_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_inv_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_inv_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    done = true;
-    return cudaSuccess;
-}
-
 template <typename R>
 cudaError_t fwd_fft(const pd_plan* p, const R* x, cplx_t<R>* grid, cudaStream_t s) {
     using C2 = cplx_t<R>;
-    cudaError_t e = set_smem_attrs<R>();
-    if (e) return e;
     const PassCfg c = pass_cfg<R>(p);
+    cudaError_t e;
+    if ((e = ensure_smem(k_fwd_rows<R>, c.smem_rows))) return e;
+    if ((e = ensure_smem(k_fwd_cols<R>, c.smem_cols))) return e;
     const int nx = p->g.nx, ny = p->g.ny;
     C2* t1 = (C2*)p->t1;
+    prof_mark(PH_FWD_ROWS, 0, s);
     k_fwd_rows<R><<<ny / c.rows_per_cta, c.threads_rows, c.smem_rows, s>>>(
         x, t1, (const R*)p->cx, (const R*)p->cy, (const C2*)p->twx, nx, ny, c.rows_per_cta);
+    prof_mark(PH_FWD_ROWS, 1, s);
+    prof_mark(PH_FWD_COLS, 0, s);
     k_fwd_cols<R><<<(p->g.Kx / 4) * (4 / c.cols_per_cta), c.threads_cols, c.smem_cols, s>>>(
         t1, grid, (const C2*)p->twy, ny, c.cols_per_cta);
+    prof_mark(PH_FWD_COLS, 1, s);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t inv_fft(const pd_plan* p, const cplx_t<R>* grid, R* out, const PrimalArgs* pa, cudaStream_t s) {
     using C2 = cplx_t<R>;
-    cudaError_t e = set_smem_attrs<R>();
-    if (e) return e;
     const PassCfg c = pass_cfg<R>(p);
+    cudaError_t e;
+    if ((e = ensure_smem(k_inv_cols<R>, c.smem_cols))) return e;
+    if ((e = ensure_smem(k_inv_rows<R>, c.smem_rows))) return e;
     const int nx = p->g.nx, ny = p->g.ny;
     C2* t1 = (C2*)p->t1;
+    prof_mark(PH_INV_COLS, 0, s);
     k_inv_cols<R><<<(p->g.Kx / 4) * (4 / c.cols_per_cta), c.threads_cols, c.smem_cols, s>>>(
         grid, t1, (const C2*)p->twy, ny, c.cols_per_cta);
+    prof_mark(PH_INV_COLS, 1, s);
+    prof_mark(PH_INV_ROWS, 0, s);
     if (pa == nullptr) {
         k_inv_rows<R><<<ny / c.rows_per_cta, c.threads_rows, c.smem_rows, s>>>(
             t1, out, (const R*)p->cx, (const R*)p->cy, (const C2*)p->twx, nx, ny, c.rows_per_cta, 0, R(0), R(0),
@@ -345,6 +341,7 @@ cudaError_t inv_fft(const pd_plan* p, const cplx_t<R>* grid, R* out, const Prima
             t1, nullptr, (const R*)p->cx, (const R*)p->cy, (const C2*)p->twx, nx, ny, c.rows_per_cta, 1,
             (R)pa->tau, (R)pa->sigma, (R)pa->varsigma, (R*)pa->x, (R*)pa->xt, (const R*)pa->st, pa->part);
     }
+    prof_mark(PH_INV_ROWS, 1, s);
     return cudaGetLastError();
 }
 

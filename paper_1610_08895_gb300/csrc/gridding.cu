@@ -278,18 +278,22 @@ cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs&
     const Geo& g = p->g;
     const R toj = R(2.0 / g.J), beta = R(g.beta);
     const int ctas = (int)std::min<int64_t>(p->nchunk, (int64_t)p->num_sms * 8);
+    prof_mark(PH_DEGRID, 0, s);
     PD_J_DISPATCH(g.J, (k_degrid_dual<R, JJ><<<ctas, 256, 0, s>>>(
         grid, (const cplx_t<R>*)a.y, (const cplx_t<R>*)a.v, (cplx_t<R>*)p->rbuf, p->cell, (const R*)p->fx,
         (const R*)p->fy, p->chunk_start, p->chunk_end, chunks, counts, p->chunk_part, g.Kx, g.Ky, toj, beta)));
+    prof_mark(PH_DEGRID, 1, s);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
+    prof_mark(PH_NORMS, 0, s);
     k_block_norms<R><<<(p->d + 127) / 128, 128, 0, s>>>(p->chunk_part, p->block_chunk_start, a.block_active, a.eps,
                                                        p->blk_norm, (R*)p->blk_scale, a.res_norm, p->d);
+    prof_mark(PH_NORMS, 1, s);
     return cudaGetLastError();
 }
 
 template <typename R, int J, int MODE> static cudaError_t grid_attr(size_t smem) {
-    return cudaFuncSetAttribute(k_grid<R, J, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return ensure_smem(k_grid<R, J, MODE>, smem);
 }
 
 template <typename R>
@@ -301,6 +305,7 @@ static cudaError_t launch_grid(const pd_plan* p, int mode, const cplx_t<R>* src,
     const size_t smem = (size_t)2 * g.ext * g.ext * sizeof(R);
     const int ctas = std::min(g.ntiles, p->num_sms * 4);
     cudaError_t e = cudaSuccess;
+    prof_mark(PH_GRID, 0, s);
     if (mode == 0) {
         PD_J_DISPATCH(g.J, (e = grid_attr<R, JJ, 0>(smem),
                             e ? (void)0 : (void)(k_grid<R, JJ, 0><<<ctas, 256, smem, s>>>(
@@ -315,9 +320,12 @@ static cudaError_t launch_grid(const pd_plan* p, int mode, const cplx_t<R>* src,
                                 p->seg_block, p->tile_seg_start, tiles, counts, U, (cplx_t<R>*)p->ringbuf, g, toj,
                                 beta))));
     }
+    prof_mark(PH_GRID, 1, s);
     if (e) return e;
     if ((e = cudaGetLastError())) return e;
+    prof_mark(PH_HALO, 0, s);
     k_halo_merge<R><<<std::min(g.ntiles, p->num_sms * 8), 256, 0, s>>>(U, (const cplx_t<R>*)p->ringbuf, flags, g);
+    prof_mark(PH_HALO, 1, s);
     return cudaGetLastError();
 }
 

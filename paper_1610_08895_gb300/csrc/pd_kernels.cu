@@ -156,10 +156,12 @@ __global__ void __launch_bounds__(SEL_NT) k_select(
 }
 
 cudaError_t select_active(const pd_plan* p, pd_state* st, const SelectArgs& a, cudaStream_t s) {
+    prof_mark(PH_SELECT, 0, s);
     k_select<<<1, SEL_NT, 0, s>>>(a.seed, a.adaptive, a.n, a.p_min, a.p_max, st->t, st->p_block, st->p_basis,
                                  st->res_norm, st->eps, p->d, p->b, st->block_active, st->basis_active,
                                  p->block_chunk_start, st->act_chunks, p->tile_seg_start, p->seg_block, p->g.ntiles,
                                  st->tile_active, st->act_tiles, st->counts);
+    prof_mark(PH_SELECT, 1, s);
     return cudaGetLastError();
 }
 
@@ -174,7 +176,9 @@ __global__ void k_sum_pairs(const double* __restrict__ part, int n, double* __re
 }
 
 cudaError_t primal_finish(const pd_plan* p, pd_state* st, cudaStream_t s) {
+    prof_mark(PH_FINISH, 0, s);
     k_sum_pairs<<<1, 256, 0, s>>>(st->prim_part, inv_rows_ctas(p), st->diag);
+    prof_mark(PH_FINISH, 1, s);
     return cudaGetLastError();
 }
 

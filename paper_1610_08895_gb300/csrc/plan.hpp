@@ -129,10 +129,24 @@ struct pd_state {
     // CUDA graph of one iteration
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gkey;
-    cudaStream_t gstream = nullptr;
+    cudaStream_t gstream = nullptr;    // private stream the graph is captured on and replayed on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // per-phase timing (pd_params.profile)
+    cudaEvent_t prof_ev[2 * 12] = {};
+    double prof_ms[12] = {};
+    int64_t prof_n[12] = {};
 };
 
 namespace pdgb {
+
+// Kernel phases of one iteration, for optional per-phase CUDA-event timing.
+enum Phase {
+    PH_SELECT = 0, PH_FWD_ROWS, PH_FWD_COLS, PH_DEGRID, PH_NORMS, PH_GRID, PH_HALO, PH_ANALYSIS,
+    PH_SYNTHESIS, PH_INV_COLS, PH_INV_ROWS, PH_FINISH, PH_COUNT
+};
+// Record the start (end = 0) or end (end = 1) event of a phase on stream s when the
+// calling thread has profiling switched on; otherwise a no-op.
+void prof_mark(int phase, int end, cudaStream_t s);
 
 // ---- fft.cu
 template <typename R>

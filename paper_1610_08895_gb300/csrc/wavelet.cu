@@ -275,25 +275,10 @@ template <typename R> static size_t syn_smem(int ty, int tx) {
     return (size_t)(4 * NKy * NKx + 2 * ty * NKx + ty * tx) * sizeof(R);
 }
 
-template <typename R> static cudaError_t wav_attrs() {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    const int big = 200 * 1024;
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_dwt_level<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_dwt_level<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_idwt_level<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_idwt_final<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_idwt_final<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    done = true;
-    return cudaSuccess;
-}
-
 template <typename R>
 static cudaError_t analysis(const pd_plan* p, const R* x, R* out, R* ds, const int32_t* active, int mode, R alpha,
                             cudaStream_t s) {
-    cudaError_t e = wav_attrs<R>();
-    if (e) return e;
+    cudaError_t e;
     const int ny = p->g.ny, nx = p->g.nx, b = p->b, L = p->L;
     const R scale = R(1.0 / std::sqrt((double)b));
     const int64_t n = (int64_t)ny * nx;
@@ -311,6 +296,7 @@ static cudaError_t analysis(const pd_plan* p, const R* x, R* out, R* ds, const i
         const R* llin = (const R*)p->ll[(lev + 1) & 1];
         R* llout = (R*)p->ll[lev & 1];
         const size_t sm = ana_smem<R>(ty, tx);
+        if ((e = ensure_smem(k_dwt_level<R, 0>, sm)) || (e = ensure_smem(k_dwt_level<R, 1>, sm))) return e;
         if (mode == 0)
             k_dwt_level<R, 0><<<grid, NT_W, sm, s>>>(x, llin, llout, out, nullptr, (const R*)p->filt, p->filt_len,
                                                      active, lev, L, ny, nx, scale, alpha);
@@ -325,8 +311,7 @@ static cudaError_t analysis(const pd_plan* p, const R* x, R* out, R* ds, const i
 template <typename R>
 static cudaError_t synthesis(const pd_plan* p, const R* coef, R* out, const int32_t* active, int mode,
                              cudaStream_t s) {
-    cudaError_t e = wav_attrs<R>();
-    if (e) return e;
+    cudaError_t e;
     const int ny = p->g.ny, nx = p->g.nx, b = p->b, L = p->L;
     const R scale = R(1.0 / std::sqrt((double)b));
     if (p->n_wavelet > 0) {
@@ -334,6 +319,7 @@ static cudaError_t synthesis(const pd_plan* p, const R* coef, R* out, const int3
             const int my = ny >> lev, mx = nx >> lev;
             const int ty = std::min(ST, my), tx = std::min(ST, mx);
             dim3 grid((mx + tx - 1) / tx, (my + ty - 1) / ty, b);
+            if ((e = ensure_smem(k_idwt_level<R>, syn_smem<R>(ty, tx)))) return e;
             k_idwt_level<R><<<grid, NT_W, syn_smem<R>(ty, tx), s>>>(
                 coef, (const R*)p->ll[(lev + 1) & 1], (R*)p->ll[lev & 1], (const R*)p->filt, p->filt_len,
                 mode == 1 ? active : nullptr, lev, L, ny, nx);
@@ -342,6 +328,9 @@ static cudaError_t synthesis(const pd_plan* p, const R* coef, R* out, const int3
     }
     const int ty = std::min(ST, ny), tx = std::min(ST, nx);
     dim3 grid((nx + tx - 1) / tx, (ny + ty - 1) / ty, 1);
+    if ((e = ensure_smem(k_idwt_final<R, 0>, syn_smem<R>(ty, tx))) ||
+        (e = ensure_smem(k_idwt_final<R, 1>, syn_smem<R>(ty, tx))))
+        return e;
     if (mode == 0)
         k_idwt_final<R, 0><<<grid, NT_W, syn_smem<R>(ty, tx), s>>>(coef, (const R*)p->ll[1], out, (const R*)p->filt,
                                                                    p->filt_len, active, b, L, ny, nx, scale);
@@ -364,9 +353,14 @@ cudaError_t psi_plain(const pd_plan* p, const R* coeffs, R* x, cudaStream_t s) {
 template <typename R>
 cudaError_t sparsity_dual(const pd_plan* p, const R* xt, R* s, R* st, const int32_t* basis_active, double alpha,
                           cudaStream_t str) {
+    prof_mark(PH_ANALYSIS, 0, str);
     cudaError_t e = analysis<R>(p, xt, s, (R*)p->ds, basis_active, 1, (R)alpha, str);
+    prof_mark(PH_ANALYSIS, 1, str);
     if (e) return e;
-    return synthesis<R>(p, (const R*)p->ds, st, basis_active, 1, str);
+    prof_mark(PH_SYNTHESIS, 0, str);
+    e = synthesis<R>(p, (const R*)p->ds, st, basis_active, 1, str);
+    prof_mark(PH_SYNTHESIS, 1, str);
+    return e;
 }
 
 template cudaError_t psi_adj_plain<float>(const pd_plan*, const float*, float*, cudaStream_t);
