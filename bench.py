@@ -27,6 +27,9 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "c5": dict(n=2048, m=16_777_216, nannuli=32, nsectors=8, J=8, bases=list(range(9)), levels=4, p=0.5,
                snr=30.0),
+    # c5 shrunk 4x (profiling captures: inputs still larger than L2, ~0.3 GB on the device)
+    "c5_div4": dict(n=1024, m=4_194_304, nannuli=32, nsectors=8, J=8, bases=list(range(9)), levels=4, p=0.5,
+                    snr=30.0),
     # the reference arm and the CPU baseline run the oracle on this 16x smaller version of c5
     "c5_div16": dict(n=512, m=1_048_576, nannuli=32, nsectors=8, J=8, bases=list(range(9)), levels=4, p=0.5,
                      snr=30.0),

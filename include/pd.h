@@ -105,11 +105,11 @@ const char* pd_last_error(void);
 /*
  * Plan facts, host outputs (any pointer may be NULL):
  * grid size (Ky, Kx), the Kaiser-Bessel beta in use, the tile edge, the number
- * of (tile, block) segments and of degridding chunks, and bytes of device
- * memory the plan holds.
+ * of (tile, block) segments, the number of tiles holding visibilities, and
+ * bytes of device memory the plan holds.
  */
 pd_status pd_plan_info(const pd_plan* plan, int32_t* ky, int32_t* kx, double* beta,
-                       int32_t* tile, int64_t* nsegments, int64_t* nchunks,
+                       int32_t* tile, int64_t* nsegments, int64_t* ntiles_nonempty,
                        int64_t* device_bytes);
 
 /* Daubechies low-pass filter of basis id k (1..8) as derived by the plan,
@@ -220,8 +220,8 @@ pd_status pd_state_get_v(const pd_plan* plan, const pd_state* st, void* v, void*
  * [nblocks], may be NULL), current block probabilities (host [nblocks], may be
  * NULL) and the activity of the last draw (host int32 [nblocks] and
  * [nbases], may be NULL), and the size of the last iteration's work lists (host
- * int32 [2]: degridding chunks of active blocks, tiles holding an active block;
- * may be NULL).
+ * int32 [2]: (tile, block) segments of active blocks, tiles holding an active
+ * block; may be NULL).
  */
 pd_status pd_state_report(const pd_plan* plan, const pd_state* st, int64_t* t, double* dx2,
                           double* x2, double* res_norm, double* p_block, int32_t* block_active,

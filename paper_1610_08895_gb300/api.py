@@ -71,7 +71,7 @@ class Plan:
         B.call("pd_plan_info", self._h, ctypes.byref(ky), ctypes.byref(kx), ctypes.byref(beta),
                ctypes.byref(tile), ctypes.byref(ns), ctypes.byref(nc), ctypes.byref(nb))
         return {"ky": ky.value, "kx": kx.value, "beta": beta.value, "tile": tile.value,
-                "nsegments": ns.value, "nchunks": nc.value, "device_bytes": nb.value}
+                "nsegments": ns.value, "ntiles_nonempty": nc.value, "device_bytes": nb.value}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -214,7 +214,7 @@ class State:
                res.ctypes.data, pb.ctypes.data, ba.ctypes.data, sa.ctypes.data, work.ctypes.data, _stream())
         return {"t": t.value, "dx2": dx2.value, "x2": x2.value, "res_norm": res, "p_block": pb,
                 "block_active": ba.astype(bool), "basis_active": sa.astype(bool),
-                "active_chunks": int(work[0]), "active_tiles": int(work[1])}
+                "active_segments": int(work[0]), "active_tiles": int(work[1])}
 
     def profile(self, reset=False):
         """{phase name: (total ms, iterations)} from iterations run with profile=True."""

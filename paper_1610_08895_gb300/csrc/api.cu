@@ -218,25 +218,31 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
                 tile_seg_start[t] = (int32_t)s;
             }
         }
-        // chunks in block-major order
-        std::vector<std::vector<int32_t>> segs_of(p->d);
-        for (int64_t s = 0; s < p->nseg; ++s) segs_of[seg_block[s]].push_back((int32_t)s);
-        std::vector<int32_t> cs, ce, cb, bcs(p->d + 1, 0);
-        for (int i = 0; i < p->d; ++i) {
-            bcs[i] = (int32_t)cs.size();
-            for (int32_t s : segs_of[i])
-                for (int32_t a = seg_start[s]; a < seg_start[s + 1]; a += CHUNK) {
-                    cs.push_back(a);
-                    ce.push_back(std::min(a + CHUNK, seg_start[s + 1]));
-                    cb.push_back(i);
-                }
+        // within each segment, row-major order of the base cell (stable: ties keep user order)
+        for (int64_t sg = 0; sg < p->nseg; ++sg)
+            std::stable_sort(order.begin() + seg_start[sg], order.begin() + seg_start[sg + 1],
+                             [&](int32_t a, int32_t b2) {
+                                 return (by[a] != by[b2]) ? by[a] < by[b2] : bx[a] < bx[b2];
+                             });
+        // segments of each block (tile order) for the fixed-order block reductions
+        std::vector<int32_t> bss(p->d + 1, 0), bsl(p->nseg);
+        for (int64_t sg = 0; sg < p->nseg; ++sg) bss[seg_block[sg] + 1]++;
+        for (int i = 0; i < p->d; ++i) bss[i + 1] += bss[i];
+        {
+            std::vector<int32_t> fill(bss.begin(), bss.end() - 1);
+            for (int64_t sg = 0; sg < p->nseg; ++sg) bsl[fill[seg_block[sg]]++] = (int32_t)sg;
         }
-        bcs[p->d] = (int32_t)cs.size();
-        p->nchunk = (int64_t)cs.size();
-        p->h_chunk_block = cb;
-        p->h_block_chunk_start = bcs;
+        // tiles by decreasing visibility count (heaviest scheduled first)
+        std::vector<int32_t> tord(g.ntiles);
+        std::iota(tord.begin(), tord.end(), 0);
+        auto tcount = [&](int32_t t) { return seg_start[tile_seg_start[t + 1]] - seg_start[tile_seg_start[t]]; };
+        std::stable_sort(tord.begin(), tord.end(), [&](int32_t a, int32_t b2) { return tcount(a) > tcount(b2); });
+        p->ntiles_nonempty = 0;
+        for (int t = 0; t < g.ntiles; ++t) p->ntiles_nonempty += tcount(t) > 0;
         p->h_tile_seg_start = tile_seg_start;
         p->h_seg_block = seg_block;
+        p->h_block_seg_start = bss;
+        p->h_block_seg_list = bsl;
 
         auto& A = p->allocs;
         size_t& B = p->device_bytes;
@@ -244,17 +250,15 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         ALLOC(p->seg_start, seg_start.size());
         ALLOC(p->seg_block, seg_block.size());
         ALLOC(p->tile_seg_start, tile_seg_start.size());
-        ALLOC(p->chunk_start, cs.size());
-        ALLOC(p->chunk_end, ce.size());
-        ALLOC(p->chunk_block, cb.size());
-        ALLOC(p->block_chunk_start, bcs.size());
+        ALLOC(p->block_seg_start, bss.size());
+        ALLOC(p->block_seg_list, bsl.size());
+        ALLOC(p->tile_order, tord.size());
         CU(upload(p->seg_start, seg_start));
         CU(upload(p->seg_block, seg_block));
         CU(upload(p->tile_seg_start, tile_seg_start));
-        CU(upload(p->chunk_start, cs));
-        CU(upload(p->chunk_end, ce));
-        CU(upload(p->chunk_block, cb));
-        CU(upload(p->block_chunk_start, bcs));
+        CU(upload(p->block_seg_start, bss));
+        CU(upload(p->block_seg_list, bsl));
+        CU(upload(p->tile_order, tord));
     }
     auto& A = p->allocs;
     size_t& B = p->device_bytes;
@@ -277,19 +281,12 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         CU(upload_real(p->fy, fys, p->prec));
     }
     {
-        std::vector<int32_t> iota_c(p->nchunk), iota_t(g.ntiles);
-        std::iota(iota_c.begin(), iota_c.end(), 0);
-        std::iota(iota_t.begin(), iota_t.end(), 0);
-        std::vector<int32_t> counts = {(int32_t)p->nchunk, g.ntiles};
+        std::vector<int32_t> counts = {(int32_t)p->nseg, g.ntiles};
         std::vector<int32_t> ob(p->d, 1), obs(p->b, 1), ot(g.ntiles, 1);
-        ALLOC(p->all_chunks, iota_c.size());
-        ALLOC(p->all_tiles, iota_t.size());
         ALLOC(p->counts_all, 2);
         ALLOC(p->ones_block, ob.size());
         ALLOC(p->ones_basis, obs.size());
         ALLOC(p->tile_ones, ot.size());
-        CU(upload(p->all_chunks, iota_c));
-        CU(upload(p->all_tiles, iota_t));
         CU(upload(p->counts_all, counts));
         CU(upload(p->ones_block, ob));
         CU(upload(p->ones_basis, obs));
@@ -326,7 +323,7 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         CU(dalloc_bytes(A, B, &p->gridb, K * p->csz));
         CU(dalloc_bytes(A, B, &p->gridu, K * p->csz));
         CU(dalloc_bytes(A, B, &p->rbuf, (size_t)M * p->csz));
-        ALLOC(p->chunk_part, 2 * p->nchunk);
+        ALLOC(p->seg_part, 2 * std::max<int64_t>(p->nseg, 1));
         ALLOC(p->blk_norm, 2 * p->d);
         CU(dalloc_bytes(A, B, &p->blk_scale, p->d * p->rsz));
         CU(dalloc_bytes(A, B, &p->ringbuf, (size_t)g.ntiles * g.ring * p->csz));
@@ -344,14 +341,14 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
 }
 
 extern "C" pd_status pd_plan_info(const pd_plan* p, int32_t* ky, int32_t* kx, double* beta, int32_t* tile,
-                                  int64_t* nsegments, int64_t* nchunks, int64_t* device_bytes) {
+                                  int64_t* nsegments, int64_t* ntiles_nonempty, int64_t* device_bytes) {
     if (!p) return fail(PD_EINVAL, "pd_plan_info: null plan");
     if (ky) *ky = p->g.Ky;
     if (kx) *kx = p->g.Kx;
     if (beta) *beta = p->g.beta;
     if (tile) *tile = p->g.tile;
     if (nsegments) *nsegments = p->nseg;
-    if (nchunks) *nchunks = p->nchunk;
+    if (ntiles_nonempty) *ntiles_nonempty = p->ntiles_nonempty;
     if (device_bytes) *device_bytes = (int64_t)p->device_bytes;
     return PD_OK;
 }
@@ -506,7 +503,7 @@ extern "C" pd_status pd_state_create(pd_plan* p, pd_state** out) {
               !dalloc_bytes(A, B, &st->y, p->M * p->csz) && !dalloc(A, B, &st->eps, p->d) &&
               !dalloc(A, B, &st->res_norm, p->d) && !dalloc(A, B, &st->p_block, p->d) &&
               !dalloc(A, B, &st->p_basis, p->b) && !dalloc(A, B, &st->block_active, p->d) &&
-              !dalloc(A, B, &st->basis_active, p->b) && !dalloc(A, B, &st->act_chunks, p->nchunk) &&
+              !dalloc(A, B, &st->basis_active, p->b) &&
               !dalloc(A, B, &st->act_tiles, p->g.ntiles) && !dalloc(A, B, &st->tile_active, p->g.ntiles) &&
               !dalloc(A, B, &st->counts, 2) && !dalloc(A, B, &st->t, 1) && !dalloc(A, B, &st->diag, 2) &&
               !dalloc(A, B, &st->prim_part, 2 * (size_t)inv_rows_ctas(p)) && !dalloc(A, B, &st->status, 1);
@@ -559,7 +556,7 @@ static cudaError_t enqueue_iteration(pd_plan* p, pd_state* st, const pd_params* 
     if ((e = select_active(p, st, sa, s))) return e;
     if ((e = fwd_fft<R>(p, (const R*)st->xt, (cplx_t<R>*)p->gridb, s))) return e;
     DualArgs da{st->y, st->v, st->block_active, st->eps, st->res_norm};
-    if ((e = degrid_dual<R>(p, (const cplx_t<R>*)p->gridb, da, st->act_chunks, st->counts, s))) return e;
+    if ((e = degrid_dual<R>(p, (const cplx_t<R>*)p->gridb, da, st->act_tiles, st->counts, s))) return e;
     if ((e = grid_dual<R>(p, da, st->act_tiles, st->counts, st->tile_active, (cplx_t<R>*)st->u, s))) return e;
     if ((e = sparsity_dual<R>(p, (const R*)st->xt, (R*)st->s, (R*)st->st, st->basis_active,
                               prm->kappa * prm->psi_norm, s)))

@@ -4,16 +4,24 @@
 // update of Algorithm 1 step 8 (l2-ball projection, eq. proj-L2) and the
 // gridding of the dual change for step 9.
 //
-// Visibilities are stored in (tile, block) order. A point at continuous grid
-// coordinate g has base cell floor(g) (kept mod K as an integer) and fraction
-// g - floor(g) (kept in the working precision, computed in FP64 at plan time);
-// its taps are the cells floor(g) - J/2 + 1 ... floor(g) + J/2 (mod K), with
-// weight phi(fraction + J/2 - 1 - a) for tap a.
+// Visibilities are stored in (tile, block, row, column) order of their base
+// cell. A point at continuous grid coordinate g has base cell floor(g) (kept
+// mod K) and fraction g - floor(g) (working precision, computed in FP64 at plan
+// time); its taps are the cells floor(g) - J/2 + 1 ... floor(g) + J/2 (mod K),
+// with weight phi(fraction + J/2 - 1 - a) for tap a.
 //
-// Gridding uses ownership instead of global atomics: one CTA per tile
-// accumulates its visibilities in shared memory over the tile plus its halo,
-// adds the interior to U (nobody else writes it in that launch) and parks the
-// halo ring; a second launch adds each tile's neighbours' rings to its border.
+// Both directions work tile by tile (one CTA owns a T x T tile at a time) on the
+// tile plus a halo of J/2 - 1 cells before and J/2 after:
+// * degridding stages that window of the grid in shared memory and gathers from it;
+// * gridding accumulates the window in shared memory, adds the interior to U
+//   (nobody else writes it in that launch) and parks the halo ring; a second
+//   launch adds each tile's neighbours' rings to its border. No global atomics.
+//   For J = 8, each group of 64 threads gives thread (cx, cy) the one tap of
+//   every visibility whose cell is congruent to (cx, cy) mod 8: the thread keeps
+//   the running sum for that cell in registers and writes it out only when the
+//   cell changes, which the row-major order of the visibilities makes rare.
+#include <algorithm>
+
 #include "common.cuh"
 #include "plan.hpp"
 
@@ -25,89 +33,98 @@ __device__ __forceinline__ void kb_taps(R frac, R* w, R two_over_j, R beta) {
     for (int a = 0; a < J; ++a) w[a] = kb_weight<R>(frac + R(J / 2 - 1 - a), two_over_j, beta);
 }
 
-template <typename R, int J>
-__device__ __forceinline__ cplx_t<R> interp(const cplx_t<R>* __restrict__ grid, int cell, R fx, R fy, int Kx, int Ky,
-                                            R two_over_j, R beta) {
-    using C2 = cplx_t<R>;
-    R wx[J], wy[J];
-    kb_taps<R, J>(fx, wx, two_over_j, beta);
-    kb_taps<R, J>(fy, wy, two_over_j, beta);
-    const int bx = cell & 0xFFFF, by = cell >> 16;
-    C2 acc = mk<C2>(R(0), R(0));
-#pragma unroll
-    for (int b = 0; b < J; ++b) {
-        const int ky = (by - J / 2 + 1 + b) & (Ky - 1);
-        C2 rs = mk<C2>(R(0), R(0));
-#pragma unroll
-        for (int a = 0; a < J; ++a) {
-            const int kx = (bx - J / 2 + 1 + a) & (Kx - 1);
-            const C2 gv = __ldg(&grid[panel_off(ky, kx, Ky)]);
-            rs.x += wx[a] * gv.x;
-            rs.y += wx[a] * gv.y;
-        }
-        acc.x += wy[b] * rs.x;
-        acc.y += wy[b] * rs.y;
-    }
-    return acc;
-}
-
 // ---------------------------------------------------------------- degridding
-// plain: out_user[perm[m]] = (G grid)_m over all chunks
-template <typename R, int J>
-__global__ void __launch_bounds__(256) k_degrid_plain(const cplx_t<R>* __restrict__ grid, cplx_t<R>* __restrict__ out,
-                                                      const int32_t* __restrict__ cell, const R* __restrict__ fxs,
-                                                      const R* __restrict__ fys, const int32_t* __restrict__ perm,
-                                                      const int32_t* __restrict__ cstart, const int32_t* __restrict__ cend,
-                                                      int nchunk, int Kx, int Ky, R two_over_j, R beta) {
-    for (int w = blockIdx.x; w < nchunk; w += gridDim.x) {
-        const int e = cend[w];
-        for (int m = cstart[w] + threadIdx.x; m < e; m += blockDim.x)
-            out[perm[m]] = interp<R, J>(grid, cell[m], fxs[m], fys[m], Kx, Ky, two_over_j, beta);
-    }
-}
-
-// pd: r = v + G b - y for the listed chunks (all of active blocks); FP64 partial
-// sums of ||r||^2 and ||G b - y||^2 per chunk.
-template <typename R, int J>
-__global__ void __launch_bounds__(256) k_degrid_dual(const cplx_t<R>* __restrict__ grid, const cplx_t<R>* __restrict__ y,
-                                                     const cplx_t<R>* __restrict__ v, cplx_t<R>* __restrict__ rbuf,
-                                                     const int32_t* __restrict__ cell, const R* __restrict__ fxs,
-                                                     const R* __restrict__ fys, const int32_t* __restrict__ cstart,
-                                                     const int32_t* __restrict__ cend, const int32_t* __restrict__ list,
-                                                     const int32_t* __restrict__ count, double* __restrict__ part,
-                                                     int Kx, int Ky, R two_over_j, R beta) {
+// MODE 0 (plain): out_user[perm[m]] = (G grid)_m for every visibility of the listed tiles.
+// MODE 1 (pd): for active blocks r = v + G b - y, FP64 partial sums of ||r||^2 and
+// ||G b - y||^2 per (tile, block) segment.
+template <typename R, int J, int MODE>
+__global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ grid, cplx_t<R>* __restrict__ out,
+                                                const cplx_t<R>* __restrict__ y, const cplx_t<R>* __restrict__ v,
+                                                cplx_t<R>* __restrict__ rbuf, const int32_t* __restrict__ cell,
+                                                const R* __restrict__ fxs, const R* __restrict__ fys,
+                                                const int32_t* __restrict__ perm,
+                                                const int32_t* __restrict__ seg_start,
+                                                const int32_t* __restrict__ seg_block,
+                                                const int32_t* __restrict__ tile_seg_start,
+                                                const int32_t* __restrict__ active, const int32_t* __restrict__ list,
+                                                const int32_t* __restrict__ count, double* __restrict__ seg_part,
+                                                Geo g, R two_over_j, R beta) {
     using C2 = cplx_t<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* win = reinterpret_cast<C2*>(smraw);      // [ext][ext]
     __shared__ double red[32];
+    const int E = g.ext, T = g.tile, H = g.halo_lo;
     const int n = *count;
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
-        const int c = list[w];
-        const int e = cend[c];
-        double ar = 0.0, ad = 0.0;
-        for (int m = cstart[c] + threadIdx.x; m < e; m += blockDim.x) {
-            const C2 gb = interp<R, J>(grid, cell[m], fxs[m], fys[m], Kx, Ky, two_over_j, beta);
-            const C2 yy = y[m], vv = v[m];
-            const C2 d = csub(gb, yy);
-            const C2 r = cadd(vv, d);
-            rbuf[m] = r;
-            ar += (double)r.x * r.x + (double)r.y * r.y;
-            ad += (double)d.x * d.x + (double)d.y * d.y;
+        const int t = list[w];
+        const int ty = t / g.ntx, tx = t - ty * g.ntx;
+        const int oy = ty * T, ox = tx * T;
+        for (int i = threadIdx.x; i < E * E; i += blockDim.x) {
+            const int ey = i / E, ex = i - ey * E;
+            const int ky = (oy - H + ey) & (g.Ky - 1), kx = (ox - H + ex) & (g.Kx - 1);
+            win[i] = grid[panel_off(ky, kx, g.Ky)];
         }
-        const double sr = block_sum(ar, red);
-        const double sd = block_sum(ad, red);
-        if (threadIdx.x == 0) { part[2 * c] = sr; part[2 * c + 1] = sd; }
+        __syncthreads();
+        for (int sg = tile_seg_start[t]; sg < tile_seg_start[t + 1]; ++sg) {
+            if (MODE == 1 && !active[seg_block[sg]]) continue;
+            double ar = 0.0, ad = 0.0;
+            const int e = seg_start[sg + 1];
+            for (int m = seg_start[sg] + threadIdx.x; m < e; m += blockDim.x) {
+                R wx[J], wy[J];
+                kb_taps<R, J>(fxs[m], wx, two_over_j, beta);
+                kb_taps<R, J>(fys[m], wy, two_over_j, beta);
+                const int c = cell[m];
+                const C2* base = win + ((c >> 16) - oy) * E + ((c & 0xFFFF) - ox);
+                R sx = 0, sy = 0;
+#pragma unroll
+                for (int b = 0; b < J; ++b) {
+                    R rx = 0, ry = 0;
+#pragma unroll
+                    for (int a = 0; a < J; ++a) {
+                        const C2 gv = base[b * E + a];
+                        rx += wx[a] * gv.x;
+                        ry += wx[a] * gv.y;
+                    }
+                    sx += wy[b] * rx;
+                    sy += wy[b] * ry;
+                }
+                if (MODE == 0) {
+                    out[perm[m]] = mk<C2>(sx, sy);
+                } else {
+                    const C2 yy = y[m], vv = v[m];
+                    const R dx = sx - yy.x, dy = sy - yy.y;
+                    const C2 r = mk<C2>(vv.x + dx, vv.y + dy);
+                    rbuf[m] = r;
+                    ar += (double)r.x * r.x + (double)r.y * r.y;
+                    ad += (double)dx * dx + (double)dy * dy;
+                }
+            }
+            if (MODE == 1) {
+                const double sr = block_sum(ar, red);
+                const double sd = block_sum(ad, red);
+                if (threadIdx.x == 0) { seg_part[2 * sg] = sr; seg_part[2 * sg + 1] = sd; }
+            }
+        }
+        __syncthreads();
     }
 }
 
-// Per-block FP64 norms in a fixed order, the ball scale c_i = max(0, 1 - eps_i/||r_i||)
-// of step 8 (so v_new = c_i r_i = z - P_B(z)), and the residual norm for Sec. 4.
+// Per-block FP64 norms summed over the block's segments in a fixed order, the ball
+// scale c_i = max(0, 1 - eps_i/||r_i||) of step 8 (so v_new = c_i r_i = z - P_B(z)),
+// and the residual norm ||G_i b - y_i|| for the adaptive probabilities of Sec. 4.
 template <typename R>
-__global__ void k_block_norms(const double* __restrict__ part, const int32_t* __restrict__ bcs,
-                              const int32_t* __restrict__ active, const double* __restrict__ eps,
-                              double* __restrict__ bnorm, R* __restrict__ scale, double* __restrict__ res_norm, int d) {
+__global__ void k_block_norms(const double* __restrict__ part, const int32_t* __restrict__ bss,
+                              const int32_t* __restrict__ bsl, const int32_t* __restrict__ active,
+                              const double* __restrict__ eps, double* __restrict__ bnorm, R* __restrict__ scale,
+                              double* __restrict__ res_norm, int d) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d || !active[i]) return;
     double sr = 0.0, sd = 0.0;
-    for (int c = bcs[i]; c < bcs[i + 1]; ++c) { sr += part[2 * c]; sd += part[2 * c + 1]; }
+    for (int k = bss[i]; k < bss[i + 1]; ++k) {
+        const int sg = bsl[k];
+        sr += part[2 * sg];
+        sd += part[2 * sg + 1];
+    }
     bnorm[2 * i] = sr;
     bnorm[2 * i + 1] = sd;
     const double nr = sqrt(sr);
@@ -120,14 +137,49 @@ __global__ void k_block_norms(const double* __restrict__ part, const int32_t* __
 __device__ __forceinline__ int ring_index(int ey, int ex, const Geo& g) {
     const int H = g.halo_lo, A = g.halo_hi, E = g.ext, T = g.tile;
     if (ey < H) return ey * E + ex;
-    if (ey >= H + T) return (H + ey - H - T) * E + ex;
+    if (ey >= H + T) return (ey - T) * E + ex;
     const int base = (H + A) * E;
     if (ex < H) return base + (ey - H) * H + ex;
     return base + T * H + (ey - H) * A + (ex - H - T);
 }
 
-// mode 0 (plain): d = y_user[perm[m]] for every visibility, U interior overwritten.
-// mode 1 (pd): for active blocks v_new = scale_i r, d = v_new - v_old, v <- v_new, U interior += .
+// value of visibility m to grid: MODE 0 the input (user order); MODE 1 the dual change
+// v_new - v_old with v_new = scale_i r (step 8), writing v_new.
+template <typename R, int MODE>
+__device__ __forceinline__ cplx_t<R> grid_value(int m, const cplx_t<R>* __restrict__ src,
+                                                const cplx_t<R>* __restrict__ rbuf, cplx_t<R>* __restrict__ v,
+                                                const int32_t* __restrict__ perm, R sc) {
+    if (MODE == 0) return src[perm[m]];
+    const cplx_t<R> r = rbuf[m], vo = v[m];
+    const cplx_t<R> vn = cscale(r, sc);
+    v[m] = vn;
+    return csub(vn, vo);
+}
+
+// Write the tile's accumulator: interior into U (overwrite in MODE 0, add in MODE 1),
+// halo ring into the tile's ring slot.
+template <typename R, int MODE>
+__device__ __forceinline__ void store_tile(const R* acc, int t, int oy, int ox, cplx_t<R>* __restrict__ U,
+                                           cplx_t<R>* __restrict__ ring, const Geo& g) {
+    using C2 = cplx_t<R>;
+    const int H = g.halo_lo, T = g.tile, E = g.ext, EE = E * E;
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        const int iy = i / T, ix = i - iy * T;
+        const int k = (iy + H) * E + ix + H;
+        const int64_t off = panel_off(oy + iy, ox + ix, g.Ky);
+        C2 val = mk<C2>(acc[k], acc[k + EE]);
+        if (MODE == 1) val = cadd(U[off], val);
+        U[off] = val;
+    }
+    C2* rg = ring + (int64_t)t * g.ring;
+    for (int i = threadIdx.x; i < EE; i += blockDim.x) {
+        const int ey = i / E, ex = i - ey * E;
+        if (ey >= H && ey < H + T && ex >= H && ex < H + T) continue;
+        rg[ring_index(ey, ex, g)] = mk<C2>(acc[i], acc[i + EE]);
+    }
+}
+
+// Generic J: one thread per visibility, shared-memory atomics per tap.
 template <typename R, int J, int MODE>
 __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf,
                                               cplx_t<R>* __restrict__ v, const R* __restrict__ scale,
@@ -139,7 +191,6 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
                                               const int32_t* __restrict__ list, const int32_t* __restrict__ count,
                                               cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, Geo g,
                                               R two_over_j, R beta) {
-    using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
     R* acc = reinterpret_cast<R*>(smraw);   // [ext*ext] re then [ext*ext] im
     const int E = g.ext, EE = E * E;
@@ -147,7 +198,7 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int t = list[w];
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
-        const int y0 = ty * g.tile, x0 = tx * g.tile;
+        const int oy = ty * g.tile, ox = tx * g.tile;
         for (int i = threadIdx.x; i < 2 * EE; i += blockDim.x) acc[i] = R(0);
         __syncthreads();
         for (int sg = tile_seg_start[t]; sg < tile_seg_start[t + 1]; ++sg) {
@@ -155,48 +206,103 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
             const R sc = MODE == 1 ? scale[seg_block[sg]] : R(0);
             const int e = seg_start[sg + 1];
             for (int m = seg_start[sg] + threadIdx.x; m < e; m += blockDim.x) {
-                C2 dv;
-                if (MODE == 0) {
-                    dv = src[perm[m]];
-                } else {
-                    const C2 r = rbuf[m], vo = v[m];
-                    const C2 vn = cscale(r, sc);
-                    v[m] = vn;
-                    dv = csub(vn, vo);
-                }
+                const cplx_t<R> dv = grid_value<R, MODE>(m, src, rbuf, v, perm, sc);
                 R wx[J], wy[J];
                 kb_taps<R, J>(fxs[m], wx, two_over_j, beta);
                 kb_taps<R, J>(fys[m], wy, two_over_j, beta);
                 const int c = cell[m];
-                const int ex0 = (c & 0xFFFF) - x0, ey0 = (c >> 16) - y0;
+                R* rowp = acc + ((c >> 16) - oy) * E + ((c & 0xFFFF) - ox);
 #pragma unroll
                 for (int b = 0; b < J; ++b) {
                     const R wr = wy[b] * dv.x, wi = wy[b] * dv.y;
-                    R* rowp = acc + (ey0 + b) * E + ex0;
 #pragma unroll
                     for (int a = 0; a < J; ++a) {
-                        atomicAdd(rowp + a, wx[a] * wr);
-                        atomicAdd(rowp + a + EE, wx[a] * wi);
+                        atomicAdd(rowp + b * E + a, wx[a] * wr);
+                        atomicAdd(rowp + b * E + a + EE, wx[a] * wi);
                     }
                 }
             }
         }
         __syncthreads();
-        const int H = g.halo_lo, T = g.tile;
-        for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-            const int iy = i / T, ix = i - iy * T;
-            const int k = (iy + H) * E + ix + H;
-            const int64_t off = panel_off(y0 + iy, x0 + ix, g.Ky);
-            C2 val = mk<C2>(acc[k], acc[k + EE]);
-            if (MODE == 1) val = cadd(U[off], val);
-            U[off] = val;
+        store_tile<R, MODE>(acc, t, oy, ox, U, ring, g);
+        __syncthreads();
+    }
+}
+
+// J = 8: four groups of 64 threads per CTA; thread (cx, cy) of a group owns the
+// tap cell congruent to (cx, cy) mod 8 of each visibility its group processes.
+constexpr int RG_BATCH = 64;
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) k_grid8(const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf,
+                                               cplx_t<R>* __restrict__ v, const R* __restrict__ scale,
+                                               const int32_t* __restrict__ active, const int32_t* __restrict__ cell,
+                                               const R* __restrict__ fxs, const R* __restrict__ fys,
+                                               const int32_t* __restrict__ perm,
+                                               const int32_t* __restrict__ seg_start,
+                                               const int32_t* __restrict__ seg_block,
+                                               const int32_t* __restrict__ tile_seg_start,
+                                               const int32_t* __restrict__ list, const int32_t* __restrict__ count,
+                                               cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, Geo g,
+                                               R two_over_j, R beta) {
+    using C2 = cplx_t<R>;
+    constexpr int J = 8;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R* acc = reinterpret_cast<R*>(smraw);                    // [ext*ext] re, [ext*ext] im
+    __shared__ R sw[4][RG_BATCH][2 * J + 1];                 // per group: wx[8], wy[8] of each staged point
+    __shared__ C2 sd[4][RG_BATCH];
+    __shared__ int sc_cell[4][RG_BATCH];
+    const int E = g.ext, EE = E * E;
+    const int grp = threadIdx.x >> 6, lane = threadIdx.x & 63;
+    const int cx = lane & 7, cy = lane >> 3;
+    const int n = *count;
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int t = list[w];
+        const int ty = t / g.ntx, tx = t - ty * g.ntx;
+        const int oy = ty * g.tile, ox = tx * g.tile;
+        for (int i = threadIdx.x; i < 2 * EE; i += blockDim.x) acc[i] = R(0);
+        __syncthreads();
+        int cur = -1;
+        R ar = 0, ai = 0;
+        for (int sg = tile_seg_start[t]; sg < tile_seg_start[t + 1]; ++sg) {
+            if (MODE == 1 && !active[seg_block[sg]]) continue;
+            const R scv = MODE == 1 ? scale[seg_block[sg]] : R(0);
+            const int s0 = seg_start[sg], len = seg_start[sg + 1] - s0;
+            const int b0 = s0 + (int)(((int64_t)len * grp) >> 2), b1 = s0 + (int)(((int64_t)len * (grp + 1)) >> 2);
+            for (int base = b0; base < b1; base += RG_BATCH) {
+                const int cnt = min(RG_BATCH, b1 - base);
+                if (lane < cnt) {
+                    const int m = base + lane;
+                    R wx[J], wy[J];
+                    kb_taps<R, J>(fxs[m], wx, two_over_j, beta);
+                    kb_taps<R, J>(fys[m], wy, two_over_j, beta);
+#pragma unroll
+                    for (int a = 0; a < J; ++a) { sw[grp][lane][a] = wx[a]; sw[grp][lane][J + a] = wy[a]; }
+                    sd[grp][lane] = grid_value<R, MODE>(m, src, rbuf, v, perm, scv);
+                    sc_cell[grp][lane] = cell[m];
+                }
+                asm volatile("bar.sync %0, 64;" ::"r"(grp + 1));
+                for (int q = 0; q < cnt; ++q) {
+                    const int c = sc_cell[grp][q];
+                    const int bx = c & 0xFFFF, by = c >> 16;
+                    const int a = (cx - bx + 3) & 7, b = (cy - by + 3) & 7;
+                    const int key = (by - oy + b) * E + (bx - ox + a);
+                    if (key != cur) {
+                        if (cur >= 0) { atomicAdd(acc + cur, ar); atomicAdd(acc + cur + EE, ai); }
+                        cur = key;
+                        ar = 0;
+                        ai = 0;
+                    }
+                    const R wgt = sw[grp][q][a] * sw[grp][q][J + b];
+                    const C2 d = sd[grp][q];
+                    ar += wgt * d.x;
+                    ai += wgt * d.y;
+                }
+                asm volatile("bar.sync %0, 64;" ::"r"(grp + 1));
+            }
         }
-        C2* rg = ring + (int64_t)t * g.ring;
-        for (int i = threadIdx.x; i < EE; i += blockDim.x) {
-            const int ey = i / E, ex = i - ey * E;
-            if (ey >= H && ey < H + T && ex >= H && ex < H + T) continue;
-            rg[ring_index(ey, ex, g)] = mk<C2>(acc[i], acc[i + EE]);
-        }
+        if (cur >= 0) { atomicAdd(acc + cur, ar); atomicAdd(acc + cur + EE, ai); }
+        __syncthreads();
+        store_tile<R, MODE>(acc, t, oy, ox, U, ring, g);
         __syncthreads();
     }
 }
@@ -243,13 +349,8 @@ __global__ void __launch_bounds__(256) k_halo_merge(cplx_t<R>* __restrict__ U, c
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename R> static int grid_ctas(const pd_plan* p, int work) {
-    int c = p->num_sms * 8;
-    return work < c ? (work > 0 ? work : 1) : c;
-}
-
-#define PD_J_DISPATCH(J_, CALL)           \
-    switch (J_) {                         \
+#define PD_J_DISPATCH(J_, CALL)                          \
+    switch (J_) {                                        \
         case 2: { constexpr int JJ = 2; CALL; } break;   \
         case 4: { constexpr int JJ = 4; CALL; } break;   \
         case 6: { constexpr int JJ = 6; CALL; } break;   \
@@ -261,68 +362,87 @@ template <typename R> static int grid_ctas(const pd_plan* p, int work) {
         default: return cudaErrorInvalidValue;           \
     }
 
-template <typename R>
-cudaError_t degrid_plain(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out_user, cudaStream_t s) {
+template <typename R, int J, int MODE>
+static cudaError_t launch_degrid(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out, const DualArgs* a,
+                                 const int32_t* tiles, const int32_t* count, int ctas, cudaStream_t s) {
     const Geo& g = p->g;
-    const R toj = R(2.0 / g.J), beta = R(g.beta);
-    const int ctas = (int)std::min<int64_t>(p->nchunk, (int64_t)p->num_sms * 8);
-    PD_J_DISPATCH(g.J, (k_degrid_plain<R, JJ><<<ctas, 256, 0, s>>>(
-        grid, out_user, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm, p->chunk_start, p->chunk_end,
-        (int)p->nchunk, g.Kx, g.Ky, toj, beta)));
+    const size_t smem = (size_t)g.ext * g.ext * sizeof(cplx_t<R>);
+    cudaError_t e = ensure_smem(k_degrid<R, J, MODE>, smem);
+    if (e) return e;
+    k_degrid<R, J, MODE><<<ctas, 256, smem, s>>>(
+        grid, out, a ? (const cplx_t<R>*)a->y : nullptr, a ? (const cplx_t<R>*)a->v : nullptr,
+        (cplx_t<R>*)p->rbuf, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start, p->seg_block,
+        p->tile_seg_start, a ? a->block_active : nullptr, tiles, count, p->seg_part, g, R(2.0 / g.J), R(g.beta));
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs& a, const int32_t* chunks,
+cudaError_t degrid_plain(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out_user, cudaStream_t s) {
+    const int ctas = std::min(p->g.ntiles, p->num_sms * 8);
+    cudaError_t e = cudaSuccess;
+    PD_J_DISPATCH(p->g.J, (e = launch_degrid<R, JJ, 0>(p, grid, out_user, nullptr, p->tile_order,
+                                                        p->counts_all + 1, ctas, s)));
+    return e;
+}
+
+template <typename R>
+cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs& a, const int32_t* tiles,
                         const int32_t* counts, cudaStream_t s) {
-    const Geo& g = p->g;
-    const R toj = R(2.0 / g.J), beta = R(g.beta);
-    const int ctas = (int)std::min<int64_t>(p->nchunk, (int64_t)p->num_sms * 8);
+    const int ctas = std::min(p->g.ntiles, p->num_sms * 8);
+    cudaError_t e = cudaSuccess;
     prof_mark(PH_DEGRID, 0, s);
-    PD_J_DISPATCH(g.J, (k_degrid_dual<R, JJ><<<ctas, 256, 0, s>>>(
-        grid, (const cplx_t<R>*)a.y, (const cplx_t<R>*)a.v, (cplx_t<R>*)p->rbuf, p->cell, (const R*)p->fx,
-        (const R*)p->fy, p->chunk_start, p->chunk_end, chunks, counts, p->chunk_part, g.Kx, g.Ky, toj, beta)));
+    PD_J_DISPATCH(p->g.J, (e = launch_degrid<R, JJ, 1>(p, grid, nullptr, &a, tiles, counts + 1, ctas, s)));
     prof_mark(PH_DEGRID, 1, s);
-    cudaError_t e = cudaGetLastError();
     if (e) return e;
     prof_mark(PH_NORMS, 0, s);
-    k_block_norms<R><<<(p->d + 127) / 128, 128, 0, s>>>(p->chunk_part, p->block_chunk_start, a.block_active, a.eps,
-                                                       p->blk_norm, (R*)p->blk_scale, a.res_norm, p->d);
+    k_block_norms<R><<<(p->d + 127) / 128, 128, 0, s>>>(p->seg_part, p->block_seg_start, p->block_seg_list,
+                                                       a.block_active, a.eps, p->blk_norm, (R*)p->blk_scale,
+                                                       a.res_norm, p->d);
     prof_mark(PH_NORMS, 1, s);
     return cudaGetLastError();
 }
 
-template <typename R, int J, int MODE> static cudaError_t grid_attr(size_t smem) {
-    return ensure_smem(k_grid<R, J, MODE>, smem);
+template <typename R, int J, int MODE>
+static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const DualArgs* a, const int32_t* tiles,
+                                 const int32_t* count, cplx_t<R>* U, cudaStream_t s) {
+    const Geo& g = p->g;
+    const size_t smem = (size_t)2 * g.ext * g.ext * sizeof(R);
+    const R toj = R(2.0 / g.J), beta = R(g.beta);
+    const int ctas = std::min(g.ntiles, p->num_sms * 4);
+    const cplx_t<R>* rb = (const cplx_t<R>*)p->rbuf;
+    cplx_t<R>* vv = a ? (cplx_t<R>*)a->v : nullptr;
+    const int32_t* act = a ? a->block_active : nullptr;
+    cudaError_t e;
+    if constexpr (J == 8) {
+        if ((e = ensure_smem(k_grid8<R, MODE>, smem))) return e;
+        k_grid8<R, MODE><<<ctas, 256, smem, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell, (const R*)p->fx,
+                                                (const R*)p->fy, p->perm, p->seg_start, p->seg_block,
+                                                p->tile_seg_start, tiles, count, U, (cplx_t<R>*)p->ringbuf, g, toj,
+                                                beta);
+    } else {
+        if ((e = ensure_smem(k_grid<R, J, MODE>, smem))) return e;
+        k_grid<R, J, MODE><<<ctas, 256, smem, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell,
+                                                  (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start,
+                                                  p->seg_block, p->tile_seg_start, tiles, count, U,
+                                                  (cplx_t<R>*)p->ringbuf, g, toj, beta);
+    }
+    return cudaGetLastError();
 }
 
 template <typename R>
 static cudaError_t launch_grid(const pd_plan* p, int mode, const cplx_t<R>* src, const DualArgs* a,
-                               const int32_t* tiles, const int32_t* counts, const int32_t* flags, cplx_t<R>* U,
+                               const int32_t* tiles, const int32_t* count, const int32_t* flags, cplx_t<R>* U,
                                cudaStream_t s) {
     const Geo& g = p->g;
-    const R toj = R(2.0 / g.J), beta = R(g.beta);
-    const size_t smem = (size_t)2 * g.ext * g.ext * sizeof(R);
-    const int ctas = std::min(g.ntiles, p->num_sms * 4);
     cudaError_t e = cudaSuccess;
     prof_mark(PH_GRID, 0, s);
     if (mode == 0) {
-        PD_J_DISPATCH(g.J, (e = grid_attr<R, JJ, 0>(smem),
-                            e ? (void)0 : (void)(k_grid<R, JJ, 0><<<ctas, 256, smem, s>>>(
-                                src, nullptr, nullptr, nullptr, nullptr, p->cell, (const R*)p->fx, (const R*)p->fy,
-                                p->perm, p->seg_start, p->seg_block, p->tile_seg_start, tiles, counts, U,
-                                (cplx_t<R>*)p->ringbuf, g, toj, beta))));
+        PD_J_DISPATCH(g.J, (e = launch_grid_j<R, JJ, 0>(p, src, a, tiles, count, U, s)));
     } else {
-        PD_J_DISPATCH(g.J, (e = grid_attr<R, JJ, 1>(smem),
-                            e ? (void)0 : (void)(k_grid<R, JJ, 1><<<ctas, 256, smem, s>>>(
-                                nullptr, (const cplx_t<R>*)p->rbuf, (cplx_t<R>*)a->v, (const R*)p->blk_scale,
-                                a->block_active, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start,
-                                p->seg_block, p->tile_seg_start, tiles, counts, U, (cplx_t<R>*)p->ringbuf, g, toj,
-                                beta))));
+        PD_J_DISPATCH(g.J, (e = launch_grid_j<R, JJ, 1>(p, src, a, tiles, count, U, s)));
     }
     prof_mark(PH_GRID, 1, s);
     if (e) return e;
-    if ((e = cudaGetLastError())) return e;
     prof_mark(PH_HALO, 0, s);
     k_halo_merge<R><<<std::min(g.ntiles, p->num_sms * 8), 256, 0, s>>>(U, (const cplx_t<R>*)p->ringbuf, flags, g);
     prof_mark(PH_HALO, 1, s);
@@ -331,7 +451,7 @@ static cudaError_t launch_grid(const pd_plan* p, int mode, const cplx_t<R>* src,
 
 template <typename R>
 cudaError_t grid_plain(const pd_plan* p, const cplx_t<R>* y_user, cplx_t<R>* U, cudaStream_t s) {
-    return launch_grid<R>(p, 0, y_user, nullptr, p->all_tiles, p->counts_all + 1, p->tile_ones, U, s);
+    return launch_grid<R>(p, 0, y_user, nullptr, p->tile_order, p->counts_all + 1, p->tile_ones, U, s);
 }
 
 template <typename R>

@@ -39,14 +39,14 @@ __device__ int block_excl_scan(int v, int* sh, int& excl) {
 
 // Step 3: Philox draws u(seed, t, stream, index) < p for blocks (stream 0) and
 // bases (stream 1); with adaptive = 1 the block probabilities are first set by
-// eq. (prob-choice) from the current residual norms. Then the active degridding
-// chunks (block-major) and the tiles holding a visibility of an active block are
-// compacted into the lists read by the persistent kernels.
+// eq. (prob-choice) from the current residual norms. Then the tiles holding a
+// visibility of an active block are compacted, heaviest first, into the list read
+// by the persistent degridding and gridding launches.
 __global__ void __launch_bounds__(SEL_NT) k_select(
     uint64_t seed, int adaptive, double an, double pmin, double pmax, int64_t* __restrict__ tptr,
     double* __restrict__ p_block, const double* __restrict__ p_basis, const double* __restrict__ res_norm,
     const double* __restrict__ eps, int d, int b, int32_t* __restrict__ block_active,
-    int32_t* __restrict__ basis_active, const int32_t* __restrict__ block_chunk_start, int32_t* __restrict__ act_chunks,
+    int32_t* __restrict__ basis_active, const int32_t* __restrict__ tile_order,
     const int32_t* __restrict__ tile_seg_start, const int32_t* __restrict__ seg_block, int ntiles,
     int32_t* __restrict__ tile_active, int32_t* __restrict__ act_tiles, int32_t* __restrict__ counts) {
     __shared__ int shi[32];
@@ -121,37 +121,29 @@ __global__ void __launch_bounds__(SEL_NT) k_select(
     for (int i = tid; i < d; i += SEL_NT) block_active[i] = philox_uniform(seed, (uint64_t)t, 0, i) < p_block[i];
     for (int j = tid; j < b; j += SEL_NT) basis_active[j] = philox_uniform(seed, (uint64_t)t, 1, j) < p_basis[j];
     __syncthreads();
-    // active chunks, block-major: each thread owns a contiguous range of blocks
-    {
-        const int per = (d + SEL_NT - 1) / SEL_NT;
-        const int i0 = min(d, tid * per), i1 = min(d, i0 + per);
-        int mine = 0;
-        for (int i = i0; i < i1; ++i)
-            if (block_active[i]) mine += block_chunk_start[i + 1] - block_chunk_start[i];
-        int excl;
-        const int total = block_excl_scan(mine, shi, excl);
-        for (int i = i0; i < i1; ++i) {
-            if (!block_active[i]) continue;
-            for (int c = block_chunk_start[i]; c < block_chunk_start[i + 1]; ++c) act_chunks[excl++] = c;
-        }
-        if (tid == 0) counts[0] = total;
-    }
-    // active tiles
+    // active tiles, in the static heaviest-first order; count active segments too
     {
         const int per = (ntiles + SEL_NT - 1) / SEL_NT;
-        const int t0 = min(ntiles, tid * per), t1 = min(ntiles, t0 + per);
-        int mine = 0;
-        for (int tt = t0; tt < t1; ++tt) {
+        const int k0 = min(ntiles, tid * per), k1 = min(ntiles, k0 + per);
+        int mine = 0, segs = 0;
+        for (int k = k0; k < k1; ++k) {
+            const int tt = tile_order[k];
             int on = 0;
-            for (int sg = tile_seg_start[tt]; sg < tile_seg_start[tt + 1]; ++sg) on |= block_active[seg_block[sg]];
+            for (int sg = tile_seg_start[tt]; sg < tile_seg_start[tt + 1]; ++sg) {
+                const int a = block_active[seg_block[sg]];
+                on |= a;
+                segs += a;
+            }
             tile_active[tt] = on;
             mine += on;
         }
         int excl;
         const int total = block_excl_scan(mine, shi, excl);
-        for (int tt = t0; tt < t1; ++tt)
-            if (tile_active[tt]) act_tiles[excl++] = tt;
-        if (tid == 0) counts[1] = total;
+        for (int k = k0; k < k1; ++k)
+            if (tile_active[tile_order[k]]) act_tiles[excl++] = tile_order[k];
+        int sexcl;
+        const int stotal = block_excl_scan(segs, shi, sexcl);
+        if (tid == 0) { counts[0] = stotal; counts[1] = total; }
     }
 }
 
@@ -159,7 +151,7 @@ cudaError_t select_active(const pd_plan* p, pd_state* st, const SelectArgs& a, c
     prof_mark(PH_SELECT, 0, s);
     k_select<<<1, SEL_NT, 0, s>>>(a.seed, a.adaptive, a.n, a.p_min, a.p_max, st->t, st->p_block, st->p_basis,
                                  st->res_norm, st->eps, p->d, p->b, st->block_active, st->basis_active,
-                                 p->block_chunk_start, st->act_chunks, p->tile_seg_start, p->seg_block, p->g.ntiles,
+                                 p->tile_order, p->tile_seg_start, p->seg_block, p->g.ntiles,
                                  st->tile_active, st->act_tiles, st->counts);
     prof_mark(PH_SELECT, 1, s);
     return cudaGetLastError();
@@ -245,36 +237,36 @@ cudaError_t scatter_user(const pd_plan* p, const cplx_t<R>* internal, cplx_t<R>*
     return cudaGetLastError();
 }
 
-// ||y_i|| per block (= ||Phi_i x^(0) - y_i|| for x^(0) = 0): chunk partials, then
+// ||y_i|| per block (= ||Phi_i x^(0) - y_i|| for x^(0) = 0): segment partials, then
 // a fixed-order sum per block.
 template <typename R>
-__global__ void k_chunk_sq(const cplx_t<R>* __restrict__ y, const int32_t* __restrict__ cs,
-                           const int32_t* __restrict__ ce, int nchunk, double* __restrict__ part) {
+__global__ void k_seg_sq(const cplx_t<R>* __restrict__ y, const int32_t* __restrict__ seg_start, int nseg,
+                         double* __restrict__ part) {
     __shared__ double sh[32];
-    for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    for (int sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
         double a = 0.0;
-        for (int m = cs[c] + threadIdx.x; m < ce[c]; m += blockDim.x) a += (double)y[m].x * y[m].x + (double)y[m].y * y[m].y;
+        for (int m = seg_start[sg] + threadIdx.x; m < seg_start[sg + 1]; m += blockDim.x)
+            a += (double)y[m].x * y[m].x + (double)y[m].y * y[m].y;
         a = block_sum(a, sh);
-        if (threadIdx.x == 0) part[2 * c + 1] = a;
+        if (threadIdx.x == 0) part[2 * sg + 1] = a;
     }
 }
-__global__ void k_block_sqrt(const double* __restrict__ part, const int32_t* __restrict__ bcs, int d,
-                             double* __restrict__ out) {
+__global__ void k_block_sqrt(const double* __restrict__ part, const int32_t* __restrict__ bss,
+                             const int32_t* __restrict__ bsl, int d, double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d) return;
     double a = 0.0;
-    for (int c = bcs[i]; c < bcs[i + 1]; ++c) a += part[2 * c + 1];
+    for (int k = bss[i]; k < bss[i + 1]; ++k) a += part[2 * bsl[k] + 1];
     out[i] = sqrt(a);
 }
 cudaError_t init_res_norm(const pd_plan* p, pd_state* st, cudaStream_t s) {
-    const int ctas = (int)std::min<int64_t>(p->nchunk, (int64_t)p->num_sms * 8);
+    const int ctas = (int)std::min<int64_t>(std::max<int64_t>(p->nseg, 1), (int64_t)p->num_sms * 8);
     if (p->prec == PD_F64)
-        k_chunk_sq<double><<<ctas, 256, 0, s>>>((const double2*)st->y, p->chunk_start, p->chunk_end, (int)p->nchunk,
-                                                p->chunk_part);
+        k_seg_sq<double><<<ctas, 256, 0, s>>>((const double2*)st->y, p->seg_start, (int)p->nseg, p->seg_part);
     else
-        k_chunk_sq<float><<<ctas, 256, 0, s>>>((const float2*)st->y, p->chunk_start, p->chunk_end, (int)p->nchunk,
-                                               p->chunk_part);
-    k_block_sqrt<<<(p->d + 127) / 128, 128, 0, s>>>(p->chunk_part, p->block_chunk_start, p->d, st->res_norm);
+        k_seg_sq<float><<<ctas, 256, 0, s>>>((const float2*)st->y, p->seg_start, (int)p->nseg, p->seg_part);
+    k_block_sqrt<<<(p->d + 127) / 128, 128, 0, s>>>(p->seg_part, p->block_seg_start, p->block_seg_list, p->d,
+                                                    st->res_norm);
     return cudaGetLastError();
 }
 

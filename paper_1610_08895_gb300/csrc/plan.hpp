@@ -16,7 +16,6 @@ namespace pdgb {
 constexpr int PW = 4;          // panel width (complex elements) of the column-panel grid layout
 constexpr int MAX_FILTER = 16; // longest Daubechies filter (db8)
 constexpr int MAX_BASES = 16;
-constexpr int CHUNK = 1024;    // visibilities per degridding work item
 
 // Device-side view of the plan, passed by value to kernels.
 struct Geo {
@@ -47,15 +46,15 @@ struct pd_plan {
     int d, b, L;
     std::vector<int> basis_ids;
     int n_wavelet;             // bases with id > 0
-    int64_t nseg, nchunk;
+    int64_t nseg;
+    int ntiles_nonempty;
     int num_sms;
     int device;
 
     // host copies of the static tables
-    std::vector<int32_t> h_chunk_block, h_block_chunk_start;
-    std::vector<int32_t> h_tile_seg_start, h_seg_block;
+    std::vector<int32_t> h_tile_seg_start, h_seg_block, h_block_seg_start, h_block_seg_list;
 
-    // device: visibilities in internal (tile, block) order
+    // device: visibilities in internal (tile, block, row, column) order
     int32_t* cell = nullptr;       // (by << 16) | bx of floor(g), mod K
     void* fx = nullptr;            // real [M]: fractional part of g_x
     void* fy = nullptr;
@@ -63,13 +62,10 @@ struct pd_plan {
     int32_t* seg_start = nullptr;  // [nseg + 1]
     int32_t* seg_block = nullptr;  // [nseg]
     int32_t* tile_seg_start = nullptr;  // [ntiles + 1]
-    int32_t* chunk_start = nullptr;     // [nchunk] internal range, block-major order
-    int32_t* chunk_end = nullptr;
-    int32_t* chunk_block = nullptr;
-    int32_t* block_chunk_start = nullptr;  // [d + 1]
-    int32_t* all_chunks = nullptr;         // 0..nchunk-1 and its count
-    int32_t* all_tiles = nullptr;          // 0..ntiles-1
-    int32_t* counts_all = nullptr;         // {nchunk, ntiles}
+    int32_t* block_seg_start = nullptr;    // [d + 1] into block_seg_list
+    int32_t* block_seg_list = nullptr;     // [nseg] segments of each block, tile order
+    int32_t* tile_order = nullptr;         // [ntiles] tiles by decreasing visibility count
+    int32_t* counts_all = nullptr;         // {nseg, ntiles}
     int32_t* ones_block = nullptr;         // all blocks active
     int32_t* ones_basis = nullptr;
 
@@ -88,7 +84,7 @@ struct pd_plan {
     void* gridb = nullptr;         // complex [Kx/PW][Ky][PW] b~ = F Z x~
     void* gridu = nullptr;         // complex grid for the plain adjoint
     void* rbuf = nullptr;          // complex [M] residuals r = v + G b - y (internal order)
-    double* chunk_part = nullptr;  // [2 * nchunk]
+    double* seg_part = nullptr;    // [2 * nseg] per-segment FP64 partial norms
     double* blk_norm = nullptr;    // [2 * d]: ||r_i||^2, ||G_i b - y_i||^2
     void* blk_scale = nullptr;     // real [d]: max(0, 1 - eps_i / ||r_i||)
     void* ringbuf = nullptr;       // complex [ntiles][ring]
@@ -116,10 +112,9 @@ struct pd_state {
     double* p_basis = nullptr;     // [b]
     int32_t* block_active = nullptr;   // [d]
     int32_t* basis_active = nullptr;   // [b]
-    int32_t* act_chunks = nullptr;     // [nchunk]
     int32_t* act_tiles = nullptr;      // [ntiles]
     int32_t* tile_active = nullptr;    // [ntiles]: tile holds a visibility of an active block
-    int32_t* counts = nullptr;         // {active chunks, active tiles}
+    int32_t* counts = nullptr;         // {active segments, active tiles}
     int64_t* t = nullptr;              // iteration counter (device)
     double* diag = nullptr;            // [2]: ||dx||^2, ||x||^2
     double* prim_part = nullptr;       // [2 * ny / rows-per-CTA]
@@ -174,9 +169,9 @@ struct DualArgs {
 // plain degrid: out (user order) = G grid
 template <typename R>
 cudaError_t degrid_plain(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out_user, cudaStream_t s);
-// pd degrid over the listed chunks: r = v + G b - y, chunk partial norms, then block scales
+// pd degrid over the listed tiles: r = v + G b - y, segment partial norms, then block scales
 template <typename R>
-cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs& a, const int32_t* chunks,
+cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs& a, const int32_t* tiles,
                         const int32_t* counts, cudaStream_t s);
 // plain grid: U = G^T y_user (U overwritten)
 template <typename R>
