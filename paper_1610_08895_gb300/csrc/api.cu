@@ -218,12 +218,29 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
                 tile_seg_start[t] = (int32_t)s;
             }
         }
-        // within each segment, row-major order of the base cell (stable: ties keep user order)
-        for (int64_t sg = 0; sg < p->nseg; ++sg)
+        // within each segment: by super-cell, then row-major by base cell (stable: ties keep
+        // user order); record the super-cell ranges of every segment
+        p->nsc_side = std::max(1, g.tile / SC);
+        const int nsc = p->nsc_side * p->nsc_side;
+        auto scell_of = [&](int32_t m) {
+            const int ly = by[m] & (g.tile - 1), lx = bx[m] & (g.tile - 1);
+            return (ly / SC) * p->nsc_side + lx / SC;
+        };
+        std::vector<int32_t> sc_start((size_t)p->nseg * (nsc + 1));
+        for (int64_t sg = 0; sg < p->nseg; ++sg) {
             std::stable_sort(order.begin() + seg_start[sg], order.begin() + seg_start[sg + 1],
                              [&](int32_t a, int32_t b2) {
+                                 const int sa = scell_of(a), sb = scell_of(b2);
+                                 if (sa != sb) return sa < sb;
                                  return (by[a] != by[b2]) ? by[a] < by[b2] : bx[a] < bx[b2];
                              });
+            int32_t* o = &sc_start[(size_t)sg * (nsc + 1)];
+            int i = seg_start[sg];
+            for (int k = 0; k <= nsc; ++k) {
+                while (i < seg_start[sg + 1] && scell_of(order[i]) < k) ++i;
+                o[k] = i;
+            }
+        }
         // segments of each block (tile order) for the fixed-order block reductions
         std::vector<int32_t> bss(p->d + 1, 0), bsl(p->nseg);
         for (int64_t sg = 0; sg < p->nseg; ++sg) bss[seg_block[sg] + 1]++;
@@ -253,6 +270,8 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         ALLOC(p->block_seg_start, bss.size());
         ALLOC(p->block_seg_list, bsl.size());
         ALLOC(p->tile_order, tord.size());
+        ALLOC(p->seg_sc_start, sc_start.size());
+        CU(upload(p->seg_sc_start, sc_start));
         CU(upload(p->seg_start, seg_start));
         CU(upload(p->seg_block, seg_block));
         CU(upload(p->tile_seg_start, tile_seg_start));
@@ -302,6 +321,11 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         CU(upload_real(p->cy, deapodisation(g.ny, g.Ky, g.J, g.beta), p->prec));
         CU(upload_real(p->twx, twiddles(g.Kx), p->prec));
         CU(upload_real(p->twy, twiddles(g.Ky), p->prec));
+        {
+            std::vector<double> kp = kb_tap_polynomials(g.J, g.beta, KB_DEG);
+            for (int a = 0; a < g.J; ++a)
+                for (int k = 0; k <= KB_DEG; ++k) p->kbpoly.c[a][k] = (float)kp[(size_t)a * (KB_DEG + 1) + k];
+        }
         p->h_filt.assign((size_t)p->b * MAX_FILTER, 0.0);
         p->h_filt_len.assign(p->b, 0);
         for (int k = 0; k < p->b; ++k) {

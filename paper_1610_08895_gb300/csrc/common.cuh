@@ -83,9 +83,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
-// Opt a kernel in to `bytes` of dynamic shared memory (above the 48 KB default).
+// Allow a kernel `bytes` of dynamic shared memory. Static plus dynamic shared memory
+// above 48 KB needs the opt-in attribute, so it is always set to the requested size.
 template <typename K> inline cudaError_t ensure_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 

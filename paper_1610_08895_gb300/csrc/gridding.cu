@@ -4,8 +4,8 @@
 // update of Algorithm 1 step 8 (l2-ball projection, eq. proj-L2) and the
 // gridding of the dual change for step 9.
 //
-// Visibilities are stored in (tile, block, row, column) order of their base
-// cell. A point at continuous grid coordinate g has base cell floor(g) (kept
+// Visibilities are stored in (tile, block, super-cell, row, column) order of
+// their base cell. A point at continuous grid coordinate g has base cell floor(g) (kept
 // mod K) and fraction g - floor(g) (working precision, computed in FP64 at plan
 // time); its taps are the cells floor(g) - J/2 + 1 ... floor(g) + J/2 (mod K),
 // with weight phi(fraction + J/2 - 1 - a) for tap a.
@@ -16,10 +16,8 @@
 // * gridding accumulates the window in shared memory, adds the interior to U
 //   (nobody else writes it in that launch) and parks the halo ring; a second
 //   launch adds each tile's neighbours' rings to its border. No global atomics.
-//   For J = 8, each group of 64 threads gives thread (cx, cy) the one tap of
-//   every visibility whose cell is congruent to (cx, cy) mod 8: the thread keeps
-//   the running sum for that cell in registers and writes it out only when the
-//   cell changes, which the row-major order of the visibilities makes rare.
+//   For J = 8 the tile's 8 x 8 super-cells are processed in four colour phases
+//   whose footprints are disjoint, so warps update the accumulator without atomics.
 #include <algorithm>
 
 #include "common.cuh"
@@ -27,10 +25,24 @@
 
 namespace pdgb {
 
+// The J tap weights phi(frac + J/2 - 1 - a) of one axis. FP32: the plan's per-tap
+// Chebyshev interpolants (degree 10, interpolation error ~3e-11 of phi(0), below FP32
+// resolution) evaluated by Horner in x = 2 frac - 1. FP64: I0 itself.
 template <typename R, int J>
-__device__ __forceinline__ void kb_taps(R frac, R* w, R two_over_j, R beta) {
+__device__ __forceinline__ void kb_taps(R frac, R* w, R two_over_j, R beta, const KbPoly& kp) {
+    if constexpr (sizeof(R) == 4) {
+        const float x = 2.0f * frac - 1.0f;
 #pragma unroll
-    for (int a = 0; a < J; ++a) w[a] = kb_weight<R>(frac + R(J / 2 - 1 - a), two_over_j, beta);
+        for (int a = 0; a < J; ++a) {
+            float acc = kp.c[a][KB_DEG];
+#pragma unroll
+            for (int k = KB_DEG - 1; k >= 0; --k) acc = fmaf(acc, x, kp.c[a][k]);
+            w[a] = acc;
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < J; ++a) w[a] = kb_weight<R>(frac + R(J / 2 - 1 - a), two_over_j, beta);
+    }
 }
 
 // ---------------------------------------------------------------- degridding
@@ -48,7 +60,7 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                                                 const int32_t* __restrict__ tile_seg_start,
                                                 const int32_t* __restrict__ active, const int32_t* __restrict__ list,
                                                 const int32_t* __restrict__ count, double* __restrict__ seg_part,
-                                                Geo g, R two_over_j, R beta) {
+                                                Geo g, R two_over_j, R beta, const KbPoly kp) {
     using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* win = reinterpret_cast<C2*>(smraw);      // [ext][ext]
@@ -71,8 +83,8 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
             const int e = seg_start[sg + 1];
             for (int m = seg_start[sg] + threadIdx.x; m < e; m += blockDim.x) {
                 R wx[J], wy[J];
-                kb_taps<R, J>(fxs[m], wx, two_over_j, beta);
-                kb_taps<R, J>(fys[m], wy, two_over_j, beta);
+                kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
+                kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
                 const int c = cell[m];
                 const C2* base = win + ((c >> 16) - oy) * E + ((c & 0xFFFF) - ox);
                 R sx = 0, sy = 0;
@@ -190,7 +202,7 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
                                               const int32_t* __restrict__ tile_seg_start,
                                               const int32_t* __restrict__ list, const int32_t* __restrict__ count,
                                               cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, Geo g,
-                                              R two_over_j, R beta) {
+                                              R two_over_j, R beta, const KbPoly kp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     R* acc = reinterpret_cast<R*>(smraw);   // [ext*ext] re then [ext*ext] im
     const int E = g.ext, EE = E * E;
@@ -208,8 +220,8 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
             for (int m = seg_start[sg] + threadIdx.x; m < e; m += blockDim.x) {
                 const cplx_t<R> dv = grid_value<R, MODE>(m, src, rbuf, v, perm, sc);
                 R wx[J], wy[J];
-                kb_taps<R, J>(fxs[m], wx, two_over_j, beta);
-                kb_taps<R, J>(fys[m], wy, two_over_j, beta);
+                kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
+                kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
                 const int c = cell[m];
                 R* rowp = acc + ((c >> 16) - oy) * E + ((c & 0xFFFF) - ox);
 #pragma unroll
@@ -229,80 +241,100 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
     }
 }
 
-// J = 8: four groups of 64 threads per CTA; thread (cx, cy) of a group owns the
-// tap cell congruent to (cx, cy) mod 8 of each visibility its group processes.
-constexpr int RG_BATCH = 64;
+// J = 8 without atomics: the tile's 8 x 8 super-cells are processed in four colour
+// phases (row parity, column parity); in a phase the footprints of different
+// super-cells are disjoint, so each warp owns one super-cell at a time and its
+// lanes (row b = lane / 4, columns 2 (lane % 4) + {0, 1}) update the 64 cells of one
+// visibility with plain shared-memory read-modify-writes. Each warp first stages 32
+// visibilities (weights, value, cell) computed one per lane.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k_grid8(const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf,
-                                               cplx_t<R>* __restrict__ v, const R* __restrict__ scale,
-                                               const int32_t* __restrict__ active, const int32_t* __restrict__ cell,
-                                               const R* __restrict__ fxs, const R* __restrict__ fys,
-                                               const int32_t* __restrict__ perm,
-                                               const int32_t* __restrict__ seg_start,
-                                               const int32_t* __restrict__ seg_block,
-                                               const int32_t* __restrict__ tile_seg_start,
-                                               const int32_t* __restrict__ list, const int32_t* __restrict__ count,
-                                               cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, Geo g,
-                                               R two_over_j, R beta) {
+__global__ void __launch_bounds__(256) k_grid8c(const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf,
+                                                cplx_t<R>* __restrict__ v, const R* __restrict__ scale,
+                                                const int32_t* __restrict__ active, const int32_t* __restrict__ cell,
+                                                const R* __restrict__ fxs, const R* __restrict__ fys,
+                                                const int32_t* __restrict__ perm,
+                                                const int32_t* __restrict__ seg_block,
+                                                const int32_t* __restrict__ tile_seg_start,
+                                                const int32_t* __restrict__ sc_start, int nsc_side,
+                                                const int32_t* __restrict__ list, const int32_t* __restrict__ count,
+                                                cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, Geo g,
+                                                R two_over_j, R beta, const KbPoly kp) {
     using C2 = cplx_t<R>;
     constexpr int J = 8;
     extern __shared__ __align__(16) unsigned char smraw[];
-    R* acc = reinterpret_cast<R*>(smraw);                    // [ext*ext] re, [ext*ext] im
-    __shared__ R sw[4][RG_BATCH][2 * J + 1];                 // per group: wx[8], wy[8] of each staged point
-    __shared__ C2 sd[4][RG_BATCH];
-    __shared__ int sc_cell[4][RG_BATCH];
+    C2* acc = reinterpret_cast<C2*>(smraw);                  // [ext*ext] interleaved complex
+    __shared__ R sw[8][32][2 * J + 1];                       // per warp: wx[8], wy[8] of each staged point
+    __shared__ C2 sd[8][32];
+    __shared__ int scl[8][32];
     const int E = g.ext, EE = E * E;
-    const int grp = threadIdx.x >> 6, lane = threadIdx.x & 63;
-    const int cx = lane & 7, cy = lane >> 3;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int brow = lane >> 2, bcol = (lane & 3) * 2;
+    const int nwarps = blockDim.x >> 5;
+    const int nsc = nsc_side * nsc_side;
     const int n = *count;
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int t = list[w];
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
         const int oy = ty * g.tile, ox = tx * g.tile;
-        for (int i = threadIdx.x; i < 2 * EE; i += blockDim.x) acc[i] = R(0);
+        for (int i = threadIdx.x; i < EE; i += blockDim.x) acc[i] = mk<C2>(R(0), R(0));
         __syncthreads();
-        int cur = -1;
-        R ar = 0, ai = 0;
-        for (int sg = tile_seg_start[t]; sg < tile_seg_start[t + 1]; ++sg) {
-            if (MODE == 1 && !active[seg_block[sg]]) continue;
-            const R scv = MODE == 1 ? scale[seg_block[sg]] : R(0);
-            const int s0 = seg_start[sg], len = seg_start[sg + 1] - s0;
-            const int b0 = s0 + (int)(((int64_t)len * grp) >> 2), b1 = s0 + (int)(((int64_t)len * (grp + 1)) >> 2);
-            for (int base = b0; base < b1; base += RG_BATCH) {
-                const int cnt = min(RG_BATCH, b1 - base);
-                if (lane < cnt) {
-                    const int m = base + lane;
-                    R wx[J], wy[J];
-                    kb_taps<R, J>(fxs[m], wx, two_over_j, beta);
-                    kb_taps<R, J>(fys[m], wy, two_over_j, beta);
+        for (int colour = 0; colour < 4; ++colour) {
+            const int cy0 = colour >> 1, cx0 = colour & 1;
+            const int hy = (nsc_side - cy0 + 1) >> 1, hx = (nsc_side - cx0 + 1) >> 1;
+            for (int k = warp; k < hy * hx; k += nwarps) {
+                const int sc = (2 * (k / hx) + cy0) * nsc_side + 2 * (k % hx) + cx0;
+                for (int sg = tile_seg_start[t]; sg < tile_seg_start[t + 1]; ++sg) {
+                    if (MODE == 1 && !active[seg_block[sg]]) continue;
+                    const R scv = MODE == 1 ? scale[seg_block[sg]] : R(0);
+                    const int lo = sc_start[(int64_t)sg * (nsc + 1) + sc];
+                    const int hi = sc_start[(int64_t)sg * (nsc + 1) + sc + 1];
+                    for (int base = lo; base < hi; base += 32) {
+                        const int m = base + lane;
+                        if (m < hi) {
+                            R wx[J], wy[J];
+                            kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
+                            kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
 #pragma unroll
-                    for (int a = 0; a < J; ++a) { sw[grp][lane][a] = wx[a]; sw[grp][lane][J + a] = wy[a]; }
-                    sd[grp][lane] = grid_value<R, MODE>(m, src, rbuf, v, perm, scv);
-                    sc_cell[grp][lane] = cell[m];
-                }
-                asm volatile("bar.sync %0, 64;" ::"r"(grp + 1));
-                for (int q = 0; q < cnt; ++q) {
-                    const int c = sc_cell[grp][q];
-                    const int bx = c & 0xFFFF, by = c >> 16;
-                    const int a = (cx - bx + 3) & 7, b = (cy - by + 3) & 7;
-                    const int key = (by - oy + b) * E + (bx - ox + a);
-                    if (key != cur) {
-                        if (cur >= 0) { atomicAdd(acc + cur, ar); atomicAdd(acc + cur + EE, ai); }
-                        cur = key;
-                        ar = 0;
-                        ai = 0;
+                            for (int a = 0; a < J; ++a) { sw[warp][lane][a] = wx[a]; sw[warp][lane][J + a] = wy[a]; }
+                            sd[warp][lane] = grid_value<R, MODE>(m, src, rbuf, v, perm, scv);
+                            scl[warp][lane] = cell[m];
+                        }
+                        __syncwarp();
+                        const int cnt = min(32, hi - base);
+                        for (int q = 0; q < cnt; ++q) {
+                            const int c = scl[warp][q];
+                            const int ey = (c >> 16) - oy + brow, ex = (c & 0xFFFF) - ox + bcol;
+                            const R wy = sw[warp][q][J + brow];
+                            const R w0 = sw[warp][q][bcol] * wy, w1 = sw[warp][q][bcol + 1] * wy;
+                            const C2 d = sd[warp][q];
+                            C2* cp = acc + ey * E + ex;
+                            C2 a0 = cp[0], a1 = cp[1];
+                            a0.x += w0 * d.x; a0.y += w0 * d.y;
+                            a1.x += w1 * d.x; a1.y += w1 * d.y;
+                            cp[0] = a0;
+                            cp[1] = a1;
+                            __syncwarp();
+                        }
                     }
-                    const R wgt = sw[grp][q][a] * sw[grp][q][J + b];
-                    const C2 d = sd[grp][q];
-                    ar += wgt * d.x;
-                    ai += wgt * d.y;
                 }
-                asm volatile("bar.sync %0, 64;" ::"r"(grp + 1));
             }
+            __syncthreads();
         }
-        if (cur >= 0) { atomicAdd(acc + cur, ar); atomicAdd(acc + cur + EE, ai); }
-        __syncthreads();
-        store_tile<R, MODE>(acc, t, oy, ox, U, ring, g);
+        // interior into U, halo ring into the ring slot
+        const int H = g.halo_lo, T = g.tile;
+        for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+            const int iy = i / T, ix = i - iy * T;
+            const int64_t off = panel_off(oy + iy, ox + ix, g.Ky);
+            C2 val = acc[(iy + H) * E + ix + H];
+            if (MODE == 1) val = cadd(U[off], val);
+            U[off] = val;
+        }
+        C2* rg = ring + (int64_t)t * g.ring;
+        for (int i = threadIdx.x; i < EE; i += blockDim.x) {
+            const int ey = i / E, ex = i - ey * E;
+            if (ey >= H && ey < H + T && ex >= H && ex < H + T) continue;
+            rg[ring_index(ey, ex, g)] = acc[i];
+        }
         __syncthreads();
     }
 }
@@ -372,7 +404,8 @@ static cudaError_t launch_degrid(const pd_plan* p, const cplx_t<R>* grid, cplx_t
     k_degrid<R, J, MODE><<<ctas, 256, smem, s>>>(
         grid, out, a ? (const cplx_t<R>*)a->y : nullptr, a ? (const cplx_t<R>*)a->v : nullptr,
         (cplx_t<R>*)p->rbuf, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start, p->seg_block,
-        p->tile_seg_start, a ? a->block_active : nullptr, tiles, count, p->seg_part, g, R(2.0 / g.J), R(g.beta));
+        p->tile_seg_start, a ? a->block_active : nullptr, tiles, count, p->seg_part, g, R(2.0 / g.J), R(g.beta),
+        p->kbpoly);
     return cudaGetLastError();
 }
 
@@ -414,17 +447,18 @@ static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const D
     const int32_t* act = a ? a->block_active : nullptr;
     cudaError_t e;
     if constexpr (J == 8) {
-        if ((e = ensure_smem(k_grid8<R, MODE>, smem))) return e;
-        k_grid8<R, MODE><<<ctas, 256, smem, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell, (const R*)p->fx,
-                                                (const R*)p->fy, p->perm, p->seg_start, p->seg_block,
-                                                p->tile_seg_start, tiles, count, U, (cplx_t<R>*)p->ringbuf, g, toj,
-                                                beta);
+        const size_t smem8 = (size_t)g.ext * g.ext * sizeof(cplx_t<R>);
+        if ((e = ensure_smem(k_grid8c<R, MODE>, smem8))) return e;
+        k_grid8c<R, MODE><<<ctas, 256, smem8, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell,
+                                                  (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_block,
+                                                  p->tile_seg_start, p->seg_sc_start, p->nsc_side, tiles, count, U,
+                                                  (cplx_t<R>*)p->ringbuf, g, toj, beta, p->kbpoly);
     } else {
         if ((e = ensure_smem(k_grid<R, J, MODE>, smem))) return e;
         k_grid<R, J, MODE><<<ctas, 256, smem, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell,
                                                   (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start,
                                                   p->seg_block, p->tile_seg_start, tiles, count, U,
-                                                  (cplx_t<R>*)p->ringbuf, g, toj, beta);
+                                                  (cplx_t<R>*)p->ringbuf, g, toj, beta, p->kbpoly);
     }
     return cudaGetLastError();
 }

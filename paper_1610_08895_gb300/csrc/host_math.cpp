@@ -119,4 +119,43 @@ std::vector<double> twiddles(int K) {
     return t;
 }
 
+// Kaiser-Bessel weight I0(beta sqrt(1 - (2t/J)^2)), |t| <= J/2.
+static double kb_phi(double t, int J, double beta) {
+    const double u = 2.0 * t / J;
+    const double arg = 1.0 - u * u;
+    return arg >= 0 ? std::cyl_bessel_i(0.0, beta * std::sqrt(arg)) : 0.0;
+}
+
+// Chebyshev interpolation at the deg + 1 Chebyshev points of the first kind,
+// then conversion of sum_j c_j T_j(x) to monomials with T_{j+1} = 2 x T_j - T_{j-1}.
+std::vector<double> kb_tap_polynomials(int J, double beta, int deg) {
+    const int n = deg + 1;
+    std::vector<double> out((size_t)J * n, 0.0);
+    for (int a = 0; a < J; ++a) {
+        std::vector<double> fx(n), cheb(n, 0.0);
+        for (int k = 0; k < n; ++k) {
+            const double xk = std::cos(M_PI * (k + 0.5) / n);
+            fx[k] = kb_phi((xk + 1.0) / 2.0 + J / 2 - 1 - a, J, beta);
+        }
+        for (int j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += fx[k] * std::cos(M_PI * j * (k + 0.5) / n);
+            cheb[j] = (j == 0 ? 1.0 : 2.0) * acc / n;
+        }
+        std::vector<double> tm1(n, 0.0), t0(n, 0.0), mono(n, 0.0);
+        t0[0] = 1.0;                                   // T_0
+        for (int j = 0; j < n; ++j) {
+            for (int i = 0; i < n; ++i) mono[i] += cheb[j] * t0[i];
+            std::vector<double> t1(n, 0.0);            // T_{j+1} = 2 x T_j - T_{j-1}
+            for (int i = 0; i + 1 < n; ++i) t1[i + 1] += 2.0 * t0[i];
+            if (j == 0) { t1.assign(n, 0.0); if (n > 1) t1[1] = 1.0; }
+            else for (int i = 0; i < n; ++i) t1[i] -= tm1[i];
+            tm1 = t0;
+            t0 = t1;
+        }
+        for (int i = 0; i < n; ++i) out[(size_t)a * n + i] = mono[i];
+    }
+    return out;
+}
+
 }  // namespace pdgb

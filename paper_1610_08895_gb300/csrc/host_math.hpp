@@ -13,5 +13,8 @@ double kb_beta_default(int J);
 std::vector<double> deapodisation(int n, int K, int J, double beta);
 // interleaved (cos, -sin)(2 pi k / K), k in [0, K)
 std::vector<double> twiddles(int K);
+// Monomial coefficients (in x = 2 f - 1, f in [0, 1)) of the degree-`deg` Chebyshev
+// interpolant of tap a's weight phi(f + J/2 - 1 - a), for a = 0..J-1: [J][deg + 1].
+std::vector<double> kb_tap_polynomials(int J, double beta, int deg);
 
 }  // namespace pdgb

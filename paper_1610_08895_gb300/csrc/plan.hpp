@@ -29,7 +29,17 @@ struct Geo {
     int ring;       // ring cells per tile
 };
 
-struct pd_plan_impl;
+// Monomial coefficients (in x = 2 f - 1) of the per-tap Chebyshev interpolants of the
+// Kaiser-Bessel weight phi(f + J/2 - 1 - a), used by the FP32 kernels.
+constexpr int KB_DEG = 10;
+struct KbPoly {
+    float c[16][KB_DEG + 1];
+};
+
+// Super-cells of SC x SC base cells inside a tile; two super-cells of the same
+// colour (row and column parity) are >= SC apart, so for J <= SC + 1 the J x J
+// footprints of their visibilities never overlap.
+constexpr int SC = 8;
 
 // Element offset of grid cell (ky, kx) in the column-panel layout [Kx/PW][K][PW].
 __host__ __device__ __forceinline__ int64_t panel_off(int ky, int kx, int K) {
@@ -62,6 +72,9 @@ struct pd_plan {
     int32_t* seg_start = nullptr;  // [nseg + 1]
     int32_t* seg_block = nullptr;  // [nseg]
     int32_t* tile_seg_start = nullptr;  // [ntiles + 1]
+    int32_t* seg_sc_start = nullptr;       // [nseg][nsc + 1]: super-cell ranges inside each segment
+    int nsc_side = 0;                      // super-cells per tile side (tile / SC)
+    pdgb::KbPoly kbpoly{};
     int32_t* block_seg_start = nullptr;    // [d + 1] into block_seg_list
     int32_t* block_seg_list = nullptr;     // [nseg] segments of each block, tile order
     int32_t* tile_order = nullptr;         // [ntiles] tiles by decreasing visibility count
