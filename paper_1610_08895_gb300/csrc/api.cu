@@ -141,7 +141,8 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
     g.nx = d->nx; g.ny = d->ny; g.Kx = 2 * d->nx; g.Ky = 2 * d->ny;
     g.J = d->kernel_width;
     g.beta = d->kb_beta > 0 ? d->kb_beta : kb_beta_default(g.J);
-    int T = d->tile ? d->tile : 64;
+    // default tile: 32 cells (the densest tiles bound the gridding critical path)
+    int T = d->tile ? d->tile : 32;
     while (T > std::min(g.Kx, g.Ky)) T >>= 1;
     while (T < g.J) T <<= 1;
     if (T > std::min(g.Kx, g.Ky)) return fail(PD_ENOTSUP, "grid smaller than the kernel width");
@@ -218,6 +219,11 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
                 tile_seg_start[t] = (int32_t)s;
             }
         }
+        p->max_tile_segs = 0;
+        for (int t = 0; t < g.ntiles; ++t)
+            p->max_tile_segs = std::max(p->max_tile_segs, tile_seg_start[t + 1] - tile_seg_start[t]);
+        if (p->max_tile_segs > 1024)
+            return fail(PD_ENOTSUP, "more than 1024 blocks share one gridding tile; use a smaller tile");
         // within each segment: by super-cell, then row-major by base cell (stable: ties keep
         // user order); record the super-cell ranges of every segment
         p->nsc_side = std::max(1, g.tile / SC);

@@ -5,7 +5,9 @@
 // gridding of the dual change for step 9.
 //
 // Visibilities are stored in (tile, block, super-cell, row, column) order of
-// their base cell. A point at continuous grid coordinate g has base cell floor(g) (kept
+// their base cell: each (tile, block) pair is a contiguous segment. Per tile, the
+// segments of active blocks are listed in shared memory and worked on as one
+// concatenated range, so inactive blocks cost nothing and batches stay full. A point at continuous grid coordinate g has base cell floor(g) (kept
 // mod K) and fraction g - floor(g) (working precision, computed in FP64 at plan
 // time); its taps are the cells floor(g) - J/2 + 1 ... floor(g) + J/2 (mod K),
 // with weight phi(fraction + J/2 - 1 - a) for tap a.
@@ -45,10 +47,58 @@ __device__ __forceinline__ void kb_taps(R frac, R* w, R two_over_j, R beta, cons
     }
 }
 
+// ---------------------------------------------------------------- active segments
+// Warp 0 lists the tile's segments whose block is active (all of them when active is
+// null) in act_seg[0..nact) and the prefix sums of their lengths in act_pre[0..nact];
+// returns nact to every thread (the caller syncs before use).
+__device__ __forceinline__ void list_active_segments(int seg0, int nseg_t, const int32_t* __restrict__ seg_block,
+                                                     const int32_t* __restrict__ active,
+                                                     const int32_t* __restrict__ seg_start, int* act_seg,
+                                                     int* act_pre, int* nact_out) {
+    if ((threadIdx.x >> 5) != 0) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int nact = 0, total = 0;
+    for (int base = 0; base < nseg_t; base += 32) {
+        const int k = base + lane;
+        const bool ok = k < nseg_t && (active == nullptr || active[seg_block[seg0 + k]]);
+        const int len = ok ? seg_start[seg0 + k + 1] - seg_start[seg0 + k] : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        int incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (ok) {
+            const int pos = nact + __popc(bal & below);
+            act_seg[pos] = seg0 + k;
+            act_pre[pos] = total + incl - len;
+        }
+        total += __shfl_sync(0xffffffffu, incl, 31);
+        nact += __popc(bal);
+    }
+    if (lane == 0) { act_pre[nact] = total; *nact_out = nact; }
+}
+
 // ---------------------------------------------------------------- degridding
+// Warp-level segmented sum: the lanes with ok add (a, b) to their local segment ls;
+// lane 0 adds each segment's warp total into part[2 ls], part[2 ls + 1] (slots owned
+// by this warp), always in the same order.
+__device__ __forceinline__ void warp_seg_add(bool ok, int ls, double a, double b, double* part) {
+    unsigned todo = __ballot_sync(0xffffffffu, ok);
+    while (todo) {
+        const int key = __shfl_sync(0xffffffffu, ls, __ffs(todo) - 1);
+        const bool mine = ok && ls == key;
+        const unsigned mask = __ballot_sync(0xffffffffu, mine);
+        const double x = warp_sum(mine ? a : 0.0), y = warp_sum(mine ? b : 0.0);
+        if ((threadIdx.x & 31) == 0) { part[2 * key] += x; part[2 * key + 1] += y; }
+        todo &= ~mask;
+    }
+}
+
 // MODE 0 (plain): out_user[perm[m]] = (G grid)_m for every visibility of the listed tiles.
-// MODE 1 (pd): for active blocks r = v + G b - y, FP64 partial sums of ||r||^2 and
-// ||G b - y||^2 per (tile, block) segment.
+// MODE 1 (pd): for visibilities of active blocks r = v + G b - y, with FP64 sums of
+// ||r||^2 and ||G b - y||^2 per (tile, block) segment (per-warp slots, summed in warp order).
 template <typename R, int J, int MODE>
 __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ grid, cplx_t<R>* __restrict__ out,
                                                 const cplx_t<R>* __restrict__ y, const cplx_t<R>* __restrict__ v,
@@ -60,40 +110,54 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                                                 const int32_t* __restrict__ tile_seg_start,
                                                 const int32_t* __restrict__ active, const int32_t* __restrict__ list,
                                                 const int32_t* __restrict__ count, double* __restrict__ seg_part,
-                                                Geo g, R two_over_j, R beta, const KbPoly kp) {
+                                                int max_segs, Geo g, R two_over_j, R beta, const KbPoly kp) {
     using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2* win = reinterpret_cast<C2*>(smraw);      // [ext][ext]
-    __shared__ double red[32];
+    C2* win = reinterpret_cast<C2*>(smraw);                              // [ext][ext]
+    double* part = reinterpret_cast<double*>(win + g.ext * g.ext);      // [8 warps][max_segs][2]
+    int* act_seg = reinterpret_cast<int*>(part + 16 * max_segs);        // [max_segs]
+    int* act_pre = act_seg + max_segs;                                   // [max_segs + 1]
+    __shared__ int nact_s;
     const int E = g.ext, T = g.tile, H = g.halo_lo;
+    const int warp = threadIdx.x >> 5;
     const int n = *count;
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int t = list[w];
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
         const int oy = ty * T, ox = tx * T;
+        const int seg0 = tile_seg_start[t], nseg_t = tile_seg_start[t + 1] - seg0;
+        list_active_segments(seg0, nseg_t, seg_block, MODE == 1 ? active : nullptr, seg_start, act_seg, act_pre,
+                             &nact_s);
         for (int i = threadIdx.x; i < E * E; i += blockDim.x) {
             const int ey = i / E, ex = i - ey * E;
             const int ky = (oy - H + ey) & (g.Ky - 1), kx = (ox - H + ex) & (g.Kx - 1);
             win[i] = grid[panel_off(ky, kx, g.Ky)];
         }
+        if (MODE == 1)
+            for (int i = threadIdx.x; i < 16 * nseg_t; i += blockDim.x) part[i] = 0.0;
         __syncthreads();
-        for (int sg = tile_seg_start[t]; sg < tile_seg_start[t + 1]; ++sg) {
-            if (MODE == 1 && !active[seg_block[sg]]) continue;
+        const int nact = nact_s, total = act_pre[nact];
+        double* mypart = part + 2 * nseg_t * warp;
+        int j = 0;   // segment cursor: positions only grow, so it only moves forward
+        for (int base = 0; base < total; base += blockDim.x) {
+            const int pos = base + threadIdx.x;
+            const bool ok = pos < total;
             double ar = 0.0, ad = 0.0;
-            const int e = seg_start[sg + 1];
-            for (int m = seg_start[sg] + threadIdx.x; m < e; m += blockDim.x) {
+            if (ok) {
+                while (act_pre[j + 1] <= pos) ++j;
+                const int m = seg_start[act_seg[j]] + pos - act_pre[j];
                 R wx[J], wy[J];
                 kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
                 kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
                 const int c = cell[m];
-                const C2* base = win + ((c >> 16) - oy) * E + ((c & 0xFFFF) - ox);
+                const C2* bp = win + ((c >> 16) - oy) * E + ((c & 0xFFFF) - ox);
                 R sx = 0, sy = 0;
 #pragma unroll
                 for (int b = 0; b < J; ++b) {
                     R rx = 0, ry = 0;
 #pragma unroll
                     for (int a = 0; a < J; ++a) {
-                        const C2 gv = base[b * E + a];
+                        const C2 gv = bp[b * E + a];
                         rx += wx[a] * gv.x;
                         ry += wx[a] * gv.y;
                     }
@@ -107,14 +171,22 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                     const R dx = sx - yy.x, dy = sy - yy.y;
                     const C2 r = mk<C2>(vv.x + dx, vv.y + dy);
                     rbuf[m] = r;
-                    ar += (double)r.x * r.x + (double)r.y * r.y;
-                    ad += (double)dx * dx + (double)dy * dy;
+                    ar = (double)r.x * r.x + (double)r.y * r.y;
+                    ad = (double)dx * dx + (double)dy * dy;
                 }
             }
-            if (MODE == 1) {
-                const double sr = block_sum(ar, red);
-                const double sd = block_sum(ad, red);
-                if (threadIdx.x == 0) { seg_part[2 * sg] = sr; seg_part[2 * sg + 1] = sd; }
+            if (MODE == 1) warp_seg_add(ok, j, ar, ad, mypart);
+        }
+        __syncthreads();
+        if (MODE == 1) {
+            for (int k = threadIdx.x; k < nact; k += blockDim.x) {
+                double sr = 0.0, sd = 0.0;
+                for (int wp = 0; wp < (int)(blockDim.x >> 5); ++wp) {
+                    sr += part[2 * nseg_t * wp + 2 * k];
+                    sd += part[2 * nseg_t * wp + 2 * k + 1];
+                }
+                seg_part[2 * act_seg[k]] = sr;
+                seg_part[2 * act_seg[k] + 1] = sd;
             }
         }
         __syncthreads();
@@ -201,37 +273,43 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
                                               const int32_t* __restrict__ seg_block,
                                               const int32_t* __restrict__ tile_seg_start,
                                               const int32_t* __restrict__ list, const int32_t* __restrict__ count,
-                                              cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, Geo g,
-                                              R two_over_j, R beta, const KbPoly kp) {
+                                              cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, int max_segs,
+                                              Geo g, R two_over_j, R beta, const KbPoly kp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     R* acc = reinterpret_cast<R*>(smraw);   // [ext*ext] re then [ext*ext] im
+    int* act_seg = reinterpret_cast<int*>(acc + 2 * g.ext * g.ext);
+    int* act_pre = act_seg + max_segs;
+    __shared__ int nact_s;
     const int E = g.ext, EE = E * E;
     const int n = *count;
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int t = list[w];
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
         const int oy = ty * g.tile, ox = tx * g.tile;
+        const int seg0 = tile_seg_start[t], nseg_t = tile_seg_start[t + 1] - seg0;
+        list_active_segments(seg0, nseg_t, seg_block, MODE == 1 ? active : nullptr, seg_start, act_seg, act_pre,
+                             &nact_s);
         for (int i = threadIdx.x; i < 2 * EE; i += blockDim.x) acc[i] = R(0);
         __syncthreads();
-        for (int sg = tile_seg_start[t]; sg < tile_seg_start[t + 1]; ++sg) {
-            if (MODE == 1 && !active[seg_block[sg]]) continue;
-            const R sc = MODE == 1 ? scale[seg_block[sg]] : R(0);
-            const int e = seg_start[sg + 1];
-            for (int m = seg_start[sg] + threadIdx.x; m < e; m += blockDim.x) {
-                const cplx_t<R> dv = grid_value<R, MODE>(m, src, rbuf, v, perm, sc);
-                R wx[J], wy[J];
-                kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
-                kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
-                const int c = cell[m];
-                R* rowp = acc + ((c >> 16) - oy) * E + ((c & 0xFFFF) - ox);
+        const int total = act_pre[nact_s];
+        int j = 0;
+        for (int pos = threadIdx.x; pos < total; pos += blockDim.x) {
+            while (act_pre[j + 1] <= pos) ++j;
+            const int sg = act_seg[j];
+            const int m = seg_start[sg] + pos - act_pre[j];
+            const cplx_t<R> dv = grid_value<R, MODE>(m, src, rbuf, v, perm, MODE == 1 ? scale[seg_block[sg]] : R(0));
+            R wx[J], wy[J];
+            kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
+            kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
+            const int c = cell[m];
+            R* rowp = acc + ((c >> 16) - oy) * E + ((c & 0xFFFF) - ox);
 #pragma unroll
-                for (int b = 0; b < J; ++b) {
-                    const R wr = wy[b] * dv.x, wi = wy[b] * dv.y;
+            for (int b = 0; b < J; ++b) {
+                const R wr = wy[b] * dv.x, wi = wy[b] * dv.y;
 #pragma unroll
-                    for (int a = 0; a < J; ++a) {
-                        atomicAdd(rowp + b * E + a, wx[a] * wr);
-                        atomicAdd(rowp + b * E + a + EE, wx[a] * wi);
-                    }
+                for (int a = 0; a < J; ++a) {
+                    atomicAdd(rowp + b * E + a, wx[a] * wr);
+                    atomicAdd(rowp + b * E + a + EE, wx[a] * wi);
                 }
             }
         }
@@ -243,54 +321,75 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
 
 // J = 8 without atomics: the tile's 8 x 8 super-cells are processed in four colour
 // phases (row parity, column parity); in a phase the footprints of different
-// super-cells are disjoint, so each warp owns one super-cell at a time and its
-// lanes (row b = lane / 4, columns 2 (lane % 4) + {0, 1}) update the 64 cells of one
-// visibility with plain shared-memory read-modify-writes. Each warp first stages 32
-// visibilities (weights, value, cell) computed one per lane.
+// super-cells are disjoint, so each warp owns one super-cell at a time. Lane l owns
+// the cells whose (row mod 8, column mod 8) is (l / 4, 2 (l % 4) + {0, 1}): every
+// footprint holds exactly one cell of each class, so a lane updates its two cells of
+// each visibility with plain shared-memory read-modify-writes and no other lane ever
+// touches them. Each warp first stages 32 visibilities (weights, value, cell), one
+// per lane.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(256) k_grid8c(const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf,
                                                 cplx_t<R>* __restrict__ v, const R* __restrict__ scale,
                                                 const int32_t* __restrict__ active, const int32_t* __restrict__ cell,
                                                 const R* __restrict__ fxs, const R* __restrict__ fys,
                                                 const int32_t* __restrict__ perm,
+                                                const int32_t* __restrict__ seg_start,
                                                 const int32_t* __restrict__ seg_block,
                                                 const int32_t* __restrict__ tile_seg_start,
                                                 const int32_t* __restrict__ sc_start, int nsc_side,
                                                 const int32_t* __restrict__ list, const int32_t* __restrict__ count,
-                                                cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, Geo g,
-                                                R two_over_j, R beta, const KbPoly kp) {
+                                                cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, int max_segs,
+                                                Geo g, R two_over_j, R beta, const KbPoly kp) {
     using C2 = cplx_t<R>;
     constexpr int J = 8;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* acc = reinterpret_cast<C2*>(smraw);                  // [ext*ext] interleaved complex
+    int* act_seg = reinterpret_cast<int*>(acc + g.ext * g.ext);
+    int* act_pre = act_seg + max_segs;
     __shared__ R sw[8][32][2 * J + 1];                       // per warp: wx[8], wy[8] of each staged point
     __shared__ C2 sd[8][32];
     __shared__ int scl[8][32];
+    __shared__ int next_sc, nact_s;
     const int E = g.ext, EE = E * E;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int brow = lane >> 2, bcol = (lane & 3) * 2;
-    const int nwarps = blockDim.x >> 5;
+    const int lcy = lane >> 2, lcx = (lane & 3) * 2;   // this lane's cell classes (mod 8)
     const int nsc = nsc_side * nsc_side;
     const int n = *count;
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int t = list[w];
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
         const int oy = ty * g.tile, ox = tx * g.tile;
+        const int seg0 = tile_seg_start[t], nseg_t = tile_seg_start[t + 1] - seg0;
+        list_active_segments(seg0, nseg_t, seg_block, MODE == 1 ? active : nullptr, seg_start, act_seg, act_pre,
+                             &nact_s);
         for (int i = threadIdx.x; i < EE; i += blockDim.x) acc[i] = mk<C2>(R(0), R(0));
-        __syncthreads();
         for (int colour = 0; colour < 4; ++colour) {
-            const int cy0 = colour >> 1, cx0 = colour & 1;
-            const int hy = (nsc_side - cy0 + 1) >> 1, hx = (nsc_side - cx0 + 1) >> 1;
-            for (int k = warp; k < hy * hx; k += nwarps) {
-                const int sc = (2 * (k / hx) + cy0) * nsc_side + 2 * (k % hx) + cx0;
-                for (int sg = tile_seg_start[t]; sg < tile_seg_start[t + 1]; ++sg) {
-                    if (MODE == 1 && !active[seg_block[sg]]) continue;
-                    const R scv = MODE == 1 ? scale[seg_block[sg]] : R(0);
-                    const int lo = sc_start[(int64_t)sg * (nsc + 1) + sc];
-                    const int hi = sc_start[(int64_t)sg * (nsc + 1) + sc + 1];
-                    for (int base = lo; base < hi; base += 32) {
-                        const int m = base + lane;
-                        if (m < hi) {
+            const int py = colour >> 1, px = colour & 1;
+            const int hy = (nsc_side - py + 1) >> 1, hx = (nsc_side - px + 1) >> 1;
+            if (threadIdx.x == 0) next_sc = 0;
+            __syncthreads();
+            const int nact = nact_s;
+            for (;;) {
+                int k = 0;
+                if (lane == 0) k = atomicAdd(&next_sc, 1);
+                k = __shfl_sync(0xffffffffu, k, 0);
+                if (k >= hy * hx) break;
+                const int sc = (2 * (k / hx) + py) * nsc_side + 2 * (k % hx) + px;
+                int fill = 0;
+                for (int j = 0; j <= nact; ++j) {
+                    int pos = 0, end = 0;
+                    R scv = R(0);
+                    if (j < nact) {
+                        const int sg = act_seg[j];
+                        pos = sc_start[(int64_t)sg * (nsc + 1) + sc];
+                        end = sc_start[(int64_t)sg * (nsc + 1) + sc + 1];
+                        if (MODE == 1) scv = scale[seg_block[sg]];
+                    }
+                    // stage this range into the batch; process the batch when full (or at the end)
+                    while (pos < end || (j == nact && fill > 0)) {
+                        const int take = min(32 - fill, end - pos);
+                        if (take > 0 && lane >= fill && lane < fill + take) {
+                            const int m = pos + lane - fill;
                             R wx[J], wy[J];
                             kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
                             kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
@@ -299,22 +398,26 @@ __global__ void __launch_bounds__(256) k_grid8c(const cplx_t<R>* __restrict__ sr
                             sd[warp][lane] = grid_value<R, MODE>(m, src, rbuf, v, perm, scv);
                             scl[warp][lane] = cell[m];
                         }
+                        if (take > 0) { fill += take; pos += take; }
+                        if (fill < 32 && j < nact) break;
                         __syncwarp();
-                        const int cnt = min(32, hi - base);
-                        for (int q = 0; q < cnt; ++q) {
+                        for (int q = 0; q < fill; ++q) {
                             const int c = scl[warp][q];
-                            const int ey = (c >> 16) - oy + brow, ex = (c & 0xFFFF) - ox + bcol;
-                            const R wy = sw[warp][q][J + brow];
-                            const R w0 = sw[warp][q][bcol] * wy, w1 = sw[warp][q][bcol + 1] * wy;
+                            const int bx = c & 0xFFFF, by = c >> 16;
+                            const int b = (lcy - by + 3) & 7;
+                            const int a0 = (lcx - bx + 3) & 7, a1 = (lcx + 1 - bx + 3) & 7;
+                            const R wy = sw[warp][q][J + b];
+                            const R w0 = sw[warp][q][a0] * wy, w1 = sw[warp][q][a1] * wy;
                             const C2 d = sd[warp][q];
-                            C2* cp = acc + ey * E + ex;
-                            C2 a0 = cp[0], a1 = cp[1];
-                            a0.x += w0 * d.x; a0.y += w0 * d.y;
-                            a1.x += w1 * d.x; a1.y += w1 * d.y;
-                            cp[0] = a0;
-                            cp[1] = a1;
-                            __syncwarp();
+                            C2* row = acc + (by - oy + b) * E + (bx - ox);
+                            C2 v0 = row[a0], v1 = row[a1];
+                            v0.x += w0 * d.x; v0.y += w0 * d.y;
+                            v1.x += w1 * d.x; v1.y += w1 * d.y;
+                            row[a0] = v0;
+                            row[a1] = v1;
                         }
+                        __syncwarp();
+                        fill = 0;
                     }
                 }
             }
@@ -398,14 +501,16 @@ template <typename R, int J, int MODE>
 static cudaError_t launch_degrid(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out, const DualArgs* a,
                                  const int32_t* tiles, const int32_t* count, int ctas, cudaStream_t s) {
     const Geo& g = p->g;
-    const size_t smem = (size_t)g.ext * g.ext * sizeof(cplx_t<R>);
+    const int ms = std::max(p->max_tile_segs, 1);
+    const size_t smem = (size_t)g.ext * g.ext * sizeof(cplx_t<R>) + (size_t)16 * ms * sizeof(double) +
+                        (size_t)(2 * ms + 1) * sizeof(int);
     cudaError_t e = ensure_smem(k_degrid<R, J, MODE>, smem);
     if (e) return e;
     k_degrid<R, J, MODE><<<ctas, 256, smem, s>>>(
         grid, out, a ? (const cplx_t<R>*)a->y : nullptr, a ? (const cplx_t<R>*)a->v : nullptr,
         (cplx_t<R>*)p->rbuf, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start, p->seg_block,
-        p->tile_seg_start, a ? a->block_active : nullptr, tiles, count, p->seg_part, g, R(2.0 / g.J), R(g.beta),
-        p->kbpoly);
+        p->tile_seg_start, a ? a->block_active : nullptr, tiles, count, p->seg_part, ms, g, R(2.0 / g.J),
+        R(g.beta), p->kbpoly);
     return cudaGetLastError();
 }
 
@@ -439,7 +544,8 @@ template <typename R, int J, int MODE>
 static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const DualArgs* a, const int32_t* tiles,
                                  const int32_t* count, cplx_t<R>* U, cudaStream_t s) {
     const Geo& g = p->g;
-    const size_t smem = (size_t)2 * g.ext * g.ext * sizeof(R);
+    const int ms = std::max(p->max_tile_segs, 1);
+    const size_t lists = (size_t)(2 * ms + 1) * sizeof(int);
     const R toj = R(2.0 / g.J), beta = R(g.beta);
     const int ctas = std::min(g.ntiles, p->num_sms * 4);
     const cplx_t<R>* rb = (const cplx_t<R>*)p->rbuf;
@@ -447,18 +553,23 @@ static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const D
     const int32_t* act = a ? a->block_active : nullptr;
     cudaError_t e;
     if constexpr (J == 8) {
-        const size_t smem8 = (size_t)g.ext * g.ext * sizeof(cplx_t<R>);
+        const size_t smem8 = (size_t)g.ext * g.ext * sizeof(cplx_t<R>) + lists;
         if ((e = ensure_smem(k_grid8c<R, MODE>, smem8))) return e;
-        k_grid8c<R, MODE><<<ctas, 256, smem8, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell,
-                                                  (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_block,
-                                                  p->tile_seg_start, p->seg_sc_start, p->nsc_side, tiles, count, U,
-                                                  (cplx_t<R>*)p->ringbuf, g, toj, beta, p->kbpoly);
+        // one warp per super-cell of a colour phase: 4 warps for 32-cell tiles, 8 above
+        const int threads = p->nsc_side <= 4 ? 128 : 256;
+        const int ctas8 = std::min(g.ntiles, p->num_sms * (threads == 128 ? 12 : 4));
+        k_grid8c<R, MODE><<<ctas8, threads, smem8, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell,
+                                                  (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start,
+                                                  p->seg_block, p->tile_seg_start, p->seg_sc_start, p->nsc_side,
+                                                  tiles, count, U, (cplx_t<R>*)p->ringbuf, ms, g, toj, beta,
+                                                  p->kbpoly);
     } else {
+        const size_t smem = (size_t)2 * g.ext * g.ext * sizeof(R) + lists;
         if ((e = ensure_smem(k_grid<R, J, MODE>, smem))) return e;
         k_grid<R, J, MODE><<<ctas, 256, smem, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell,
                                                   (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start,
                                                   p->seg_block, p->tile_seg_start, tiles, count, U,
-                                                  (cplx_t<R>*)p->ringbuf, g, toj, beta, p->kbpoly);
+                                                  (cplx_t<R>*)p->ringbuf, ms, g, toj, beta, p->kbpoly);
     }
     return cudaGetLastError();
 }

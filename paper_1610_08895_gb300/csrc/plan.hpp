@@ -74,6 +74,7 @@ struct pd_plan {
     int32_t* tile_seg_start = nullptr;  // [ntiles + 1]
     int32_t* seg_sc_start = nullptr;       // [nseg][nsc + 1]: super-cell ranges inside each segment
     int nsc_side = 0;                      // super-cells per tile side (tile / SC)
+    int max_tile_segs = 0;                 // most (tile, block) segments in one tile
     pdgb::KbPoly kbpoly{};
     int32_t* block_seg_start = nullptr;    // [d + 1] into block_seg_list
     int32_t* block_seg_list = nullptr;     // [nseg] segments of each block, tile order
