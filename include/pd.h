@@ -137,6 +137,31 @@ pd_status pd_apply_phi_adj(pd_plan* plan, const void* y, void* x, int32_t batch,
  */
 pd_status pd_apply_psi_adj(pd_plan* plan, const void* x, void* coeffs, void* stream);
 
+/*
+ * Psi^H x without a plan and without allocating device memory (the paper has no
+ * counterpart; this is a deployment variant of pd_apply_psi_adj). For callers
+ * that cannot call cudaMalloc once they are running: code that must keep a fixed
+ * device-memory budget, or that runs where allocation is not allowed, such as
+ * between the start and end of a CUDA-graph stream capture. The output equals
+ * pd_apply_psi_adj's for the same image, bases and levels.
+ *
+ * x: device real [ny][nx]; coeffs: device real [nbases][ny][nx] (packed layout,
+ * scaled by nbases^{-1/2}); basis_ids: host [nbases] (0 = Dirac, k = db_k);
+ * precision PD_F32 / PD_F64 selects float / double data.
+ * Scratch: the library's file-scope 16 MiB device array (held by every GPU that
+ * loads the library until exit). Calls needing more than it holds -- about
+ * 2 * nbases * (ny/2) * (nx/2) elements plus the filter table -- fail with
+ * PD_EINVAL and a message naming the size. Every call shares the array, so calls
+ * that overlap on the GPU (different streams, or different host threads without
+ * ordering) race; order them on one stream.
+ * The first call on a device does a one-time set-up (looks up the array's device
+ * address with that device current, derives the Daubechies filters on the host);
+ * make that first call before any stream capture. Asynchronous on `stream`.
+ */
+pd_status pd_apply_psi_adj_noalloc(const void* x, void* coeffs, int32_t nx, int32_t ny, int32_t levels,
+                                   const int32_t* basis_ids, int32_t nbases, int32_t precision,
+                                   void* stream);
+
 /* Synthesis x = Psi coeffs = b^{-1/2} sum_j Psi_j coeffs_j (Sec. 3). */
 pd_status pd_apply_psi(pd_plan* plan, const void* coeffs, void* x, void* stream);
 

@@ -54,6 +54,8 @@ _SIGS = {
     "pd_apply_phi_adj": ([_VP, _VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
     "pd_apply_psi_adj": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "pd_apply_psi": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "pd_apply_psi_adj_noalloc": ([_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
+                                  ctypes.c_int32, _VP], ctypes.c_int),
     "pd_operator_norms": ([_VP, _VP, ctypes.c_int32, ctypes.c_double, _VP, _VP, _VP, _VP], ctypes.c_int),
     "pd_state_create": ([_VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "pd_state_destroy": ([_VP], ctypes.c_int),

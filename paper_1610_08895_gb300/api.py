@@ -236,6 +236,22 @@ class State:
         B.call("pd_state_load", self.plan.handle, self._h, buf.ctypes.data, _stream())
 
 
+def psi_adj_noalloc(x, basis_ids, levels, coeffs=None):
+    """Psi^H x through pd_apply_psi_adj_noalloc: no plan, no device allocation by the
+    library (coeffs must be passed in by callers that cannot allocate)."""
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dim() != 2 or not x.is_contiguous():
+        raise TypeError("x must be a contiguous 2-D CUDA tensor")
+    prec = {torch.float32: B.PD_F32, torch.float64: B.PD_F64}[x.dtype]
+    ids = np.ascontiguousarray(basis_ids, dtype=np.int32)
+    ny, nx = x.shape
+    if coeffs is None:
+        coeffs = torch.empty((len(ids), ny, nx), dtype=x.dtype, device=x.device)
+    _need(coeffs, x.dtype, (len(ids), ny, nx), "coeffs")
+    B.call("pd_apply_psi_adj_noalloc", _ptr(x), _ptr(coeffs), nx, ny, int(levels), ids.ctypes.data, len(ids), prec,
+           _stream())
+    return coeffs
+
+
 def daubechies_filter(k):
     """Low-pass filter of db_k as derived by the library (host)."""
     h = np.zeros(2 * k)

@@ -28,6 +28,8 @@ static pd_status fail(pd_status s, const std::string& msg) {
 
 extern "C" const char* pd_last_error(void) { return g_err.c_str(); }
 
+pd_status pdgb::set_error(pd_status st, const char* msg) { return fail(st, msg); }
+
 // ---- per-phase CUDA-event timing (pd_params.profile)
 static thread_local pd_state* g_prof = nullptr;
 

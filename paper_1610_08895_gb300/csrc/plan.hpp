@@ -156,6 +156,8 @@ enum Phase {
 // Record the start (end = 0) or end (end = 1) event of a phase on stream s when the
 // calling thread has profiling switched on; otherwise a no-op.
 void prof_mark(int phase, int end, cudaStream_t s);
+// Record `msg` as the calling thread's last error (pd_last_error) and return `st`.
+pd_status set_error(pd_status st, const char* msg);
 
 // ---- fft.cu
 template <typename R>

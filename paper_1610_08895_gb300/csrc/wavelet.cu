@@ -12,8 +12,12 @@
 // eq. prox-L1), fused into the analysis epilogue; the change ds = s_new - s_old
 // is synthesised and added to s~ (step 14) so that inactive bases cost nothing.
 #include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <string>
 
 #include "common.cuh"
+#include "host_math.hpp"
 #include "plan.hpp"
 
 namespace pdgb {
@@ -362,6 +366,144 @@ cudaError_t sparsity_dual(const pd_plan* p, const R* xt, R* s, R* st, const int3
     prof_mark(PH_SYNTHESIS, 1, str);
     return e;
 }
+
+// -------------------------------------------------------------------- allocation-free analysis
+// pd_apply_psi_adj_noalloc runs the same analysis kernels as pd_apply_psi_adj, but
+// without a plan: its scratch (the two approximation buffers of the level loop, the
+// filter table, the basis flags) lives in this file-scope device array instead of
+// memory allocated with cudaMalloc. Every GPU that loads the library holds the array
+// until exit; every call shares it.
+constexpr size_t PSI_STATIC_BYTES = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_psi_static[PSI_STATIC_BYTES];
+
+static std::mutex g_psi_static_mu;
+static void* g_psi_static_addr[64];       // device address of g_psi_static, per device
+static int g_psi_static_sms[64];
+static bool g_db_ready = false;
+static double g_db_d[9][MAX_FILTER];      // db_k low-pass filters (k = 1..8), FP64
+static float g_db_f[9][MAX_FILTER];
+
+static size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// One-time set-up for the current device: the device address of the static array (host
+// code may not use the symbol itself as a pointer) and the Daubechies table.
+static pd_status psi_static_setup(int dev, void** addr, int* sms) {
+    std::lock_guard<std::mutex> lock(g_psi_static_mu);
+    if (dev < 0 || dev >= 64) return set_error(PD_ENOTSUP, "pd_apply_psi_adj_noalloc: device index above 63");
+    if (!g_db_ready) {
+        for (int k = 1; k <= 8; ++k) {
+            const std::vector<double> h = daubechies(k);
+            for (size_t j = 0; j < h.size(); ++j) { g_db_d[k][j] = h[j]; g_db_f[k][j] = (float)h[j]; }
+        }
+        g_db_ready = true;
+    }
+    if (!g_psi_static_addr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_psi_static);
+        if (e != cudaSuccess || ptr == nullptr)
+            return set_error(PD_ECUDA, "pd_apply_psi_adj_noalloc: cudaGetSymbolAddress of the static scratch failed");
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return set_error(PD_ECUDA, "pd_apply_psi_adj_noalloc: cannot query the SM count");
+        g_psi_static_addr[dev] = ptr;
+        g_psi_static_sms[dev] = n;
+    }
+    *addr = g_psi_static_addr[dev];
+    *sms = g_psi_static_sms[dev];
+    return PD_OK;
+}
+
+template <typename R>
+static pd_status psi_adj_static_t(const R* x, R* coeffs, int nx, int ny, int L, const int32_t* ids, int b,
+                                  unsigned char* scratch, int sms, cudaStream_t s) {
+    const size_t filt_bytes = align256((size_t)b * MAX_FILTER * sizeof(R));
+    const size_t flag_bytes = align256((size_t)b * sizeof(int32_t));
+    const size_t ll_bytes = align256((size_t)b * (ny / 2) * (nx / 2) * sizeof(R));
+    R* filt = (R*)scratch;
+    int32_t* flen = (int32_t*)(scratch + filt_bytes);
+    int32_t* ones = (int32_t*)(scratch + filt_bytes + flag_bytes);
+    R* ll[2] = {(R*)(scratch + filt_bytes + 2 * flag_bytes), (R*)(scratch + filt_bytes + 2 * flag_bytes + ll_bytes)};
+    // filter table and flags for this call, copied from host arrays of fixed size
+    R hf[MAX_BASES * MAX_FILTER];
+    int32_t hl[MAX_BASES], h1[MAX_BASES];
+    int nwav = 0;
+    for (int k = 0; k < b; ++k) {
+        const int id = ids[k];
+        hl[k] = id == 0 ? 0 : 2 * id;
+        h1[k] = 1;
+        nwav += id > 0;
+        for (int j = 0; j < MAX_FILTER; ++j)
+            hf[k * MAX_FILTER + j] = id == 0 || j >= 2 * id ? R(0) : (sizeof(R) == 8 ? (R)g_db_d[id][j] : (R)g_db_f[id][j]);
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(filt, hf, (size_t)b * MAX_FILTER * sizeof(R), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(flen, hl, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(ones, h1, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, s)))
+        return set_error(PD_ECUDA, cudaGetErrorString(e));
+    // copies from pageable host memory are staged before cudaMemcpyAsync returns, so the
+    // local arrays may go out of scope without a stream synchronisation
+    const R scale = R(1.0 / std::sqrt((double)b));
+    const int64_t n = (int64_t)ny * nx;
+    const int dgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 4);
+    k_dirac<R, 0><<<dgrid, 256, 0, s>>>(x, coeffs, coeffs, flen, ones, b, n, scale, R(0));
+    if ((e = cudaGetLastError())) return set_error(PD_ECUDA, cudaGetErrorString(e));
+    if (nwav == 0) return PD_OK;
+    for (int lev = 0; lev < L; ++lev) {
+        const int hy = (ny >> lev) / 2, hx = (nx >> lev) / 2;
+        const int ty = std::min(AT, hy), tx = std::min(AT, hx);
+        dim3 grid((hx + tx - 1) / tx, (hy + ty - 1) / ty, b);
+        const size_t sm = ana_smem<R>(ty, tx);
+        if ((e = ensure_smem(k_dwt_level<R, 0>, sm))) return set_error(PD_ECUDA, cudaGetErrorString(e));
+        k_dwt_level<R, 0><<<grid, NT_W, sm, s>>>(x, ll[(lev + 1) & 1], ll[lev & 1], coeffs, nullptr, filt, flen, ones,
+                                                 lev, L, ny, nx, scale, R(0));
+        if ((e = cudaGetLastError())) return set_error(PD_ECUDA, cudaGetErrorString(e));
+    }
+    return PD_OK;
+}
+
+}  // namespace pdgb
+
+extern "C" pd_status pd_apply_psi_adj_noalloc(const void* x, void* coeffs, int32_t nx, int32_t ny, int32_t levels,
+                                              const int32_t* basis_ids, int32_t nbases, int32_t precision,
+                                              void* stream) {
+    using namespace pdgb;
+    auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+    if (!x || !coeffs || !basis_ids) return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: null pointer");
+    if (!pow2(nx) || !pow2(ny) || nx < 16 || ny < 16 || nx > 8192 || ny > 8192)
+        return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: image sides must be powers of two in [16, 8192]");
+    if (levels < 1 || (nx >> levels) < 1 || (ny >> levels) < 1)
+        return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: levels must satisfy 1 <= L and n >> L >= 1");
+    if (nbases < 1 || nbases > MAX_BASES) return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: nbases in [1, 16]");
+    for (int k = 0; k < nbases; ++k)
+        if (basis_ids[k] < 0 || basis_ids[k] > 8)
+            return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: basis ids must be 0 (Dirac) or 1..8");
+    if (precision != PD_F32 && precision != PD_F64)
+        return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: precision must be PD_F32 or PD_F64");
+    const size_t rsz = precision == PD_F64 ? 8 : 4;
+    const size_t need = align256((size_t)nbases * MAX_FILTER * rsz) + 2 * align256((size_t)nbases * 4) +
+                        2 * align256((size_t)nbases * (ny / 2) * (nx / 2) * rsz);
+    if (need > PSI_STATIC_BYTES) {
+        static thread_local char msg[160];
+        snprintf(msg, sizeof msg,
+                 "pd_apply_psi_adj_noalloc: needs %zu bytes of scratch, the static array holds %zu "
+                 "(use pd_apply_psi_adj with a plan)", need, PSI_STATIC_BYTES);
+        return set_error(PD_EINVAL, msg);
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return set_error(PD_ECUDA, "pd_apply_psi_adj_noalloc: no current device");
+    void* addr = nullptr;
+    int sms = 0;
+    pd_status st = psi_static_setup(dev, &addr, &sms);
+    if (st != PD_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return precision == PD_F64
+               ? psi_adj_static_t<double>((const double*)x, (double*)coeffs, nx, ny, levels, basis_ids, nbases,
+                                          (unsigned char*)addr, sms, s)
+               : psi_adj_static_t<float>((const float*)x, (float*)coeffs, nx, ny, levels, basis_ids, nbases,
+                                         (unsigned char*)addr, sms, s);
+}
+
+namespace pdgb {
 
 template cudaError_t psi_adj_plain<float>(const pd_plan*, const float*, float*, cudaStream_t);
 template cudaError_t psi_adj_plain<double>(const pd_plan*, const double*, double*, cudaStream_t);
