@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
@@ -268,6 +270,27 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
         st2.close()
 
+    # ---- the same workload with FP64 bulk data (the benchmark spec's FP64 comparison form)
+    fp64 = None
+    if not args.no_fp64:
+        plan64 = Plan(n, n, uv, blk, d, kernel_width=cfg["J"], basis_ids=cfg["bases"], levels=cfg["levels"],
+                      precision="f64")
+        st64 = State(plan64)
+        st64.pd_state_set_data(torch.tensor(y_host.astype(np.complex128), device="cuda"), eps)
+        st64.pd_iterate(3, use_graph=True, **kw)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        st64.pd_iterate(args.fp64_steps, use_graph=True, **kw)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        fp64 = {"value": round(args.fp64_steps / (ms64 / 1e3), 3), "unit": "PD iters/s",
+                "ms_per_step": round(ms64 / args.fp64_steps, 3), "steps": args.fp64_steps,
+                "form": "same kernels and graph with FP64 bulk data (I0 evaluated directly)"}
+        st64.close()
+        plan64.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.seed, steps=2, warmup=1)
@@ -286,7 +309,7 @@ def run_ours(args):
                        "graph": "one CUDA graph per iteration, replayed", "setup_s": round(setup_s, 1),
                        "plan": info},
             "roofline": roofline, "kernels": kernels, "clocks": clk.summary(), "e2e": e2e,
-            "cpu_baseline": cpu,
+            "fp64": fp64, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
