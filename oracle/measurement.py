@@ -162,3 +162,21 @@ class Geometry:
         """Re(Phi^H y) = Re(Z^T F^H G^T y): the adjoint of Phi as a map R^N -> C^M."""
         return np.real(self.zpad_adj(self.fft_adj(self.grid(y, uv))))
 
+    def phi_adj_at(self, y, uv, pixels):
+        """Re(Phi^H y) at the listed pixels (iy, ix), one pixel at a time.
+
+        Written out from Phi^H = Z^T F^H G^T for a single output: the entry at pixel
+        p is c_y c_x sum_m y_m A_m B_m with A_m = sum_a phi(g_x - k_a) exp(+2 pi i k_a l_x / K_x)
+        over the x taps of point m (B_m likewise in y) and l the centred coordinates.
+        Linear in the number of points; used where a full grid is too large to form.
+        """
+        bx, by, wx, wy = self._taps(uv)
+        y = np.asarray(y, dtype=np.complex128)
+        out = []
+        for iy, ix in pixels:
+            lx, ly = ix - self.nx // 2, iy - self.ny // 2
+            a = sum(wx[k] * np.exp(2j * np.pi * (bx + k) * lx / self.Kx) for k in range(self.J))
+            b = sum(wy[k] * np.exp(2j * np.pi * (by + k) * ly / self.Ky) for k in range(self.J))
+            out.append(np.real(self.cy[iy] * self.cx[ix] * np.sum(y * a * b)))
+        return np.array(out)
+

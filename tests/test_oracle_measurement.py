@@ -156,3 +156,14 @@ def test_grid_is_transpose_of_degrid_including_wrap():
                 if w and (np.floor(gx) - 3 <= kx <= np.floor(gx) + 4) and (np.floor(gy) - 3 <= ky <= np.floor(gy) + 4):
                     Gd[m, (ky % 16) * 16 + (kx % 16)] += w
     assert np.allclose(geo.degrid(b, uv), Gd @ b.ravel(), rtol=1e-13)
+
+
+def test_adjoint_at_pixels_equals_full_adjoint():
+    rng = np.random.default_rng(12)
+    geo = meas.Geometry(16, 32, 8)
+    uv = synth.uv_gaussian(400, seed=8)
+    y = rng.normal(size=400) + 1j * rng.normal(size=400)
+    full = geo.phi_adj(y, uv)
+    pix = [(0, 0), (7, 31), (15, 3), (8, 16), (3, 29)]
+    got = geo.phi_adj_at(y, uv, pix)
+    assert np.allclose(got, [full[iy, ix] for iy, ix in pix], rtol=1e-11, atol=1e-11 * np.abs(full).max())
