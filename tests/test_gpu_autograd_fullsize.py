@@ -62,7 +62,11 @@ def test_phi_autograd_gradient_oracle_and_finite_differences(precision):
         xm.view(-1)[p] -= h
         fd.append((L(xp) - L(xm)) / (2 * h))
     fd = np.array(fd)
-    tol = 1e-6 if precision == "f64" else 5e-3
+    # FP64: differences agree to rounding. FP32: the loss of an FP32 Phi carries rounding
+    # noise of order 2^-24 sum_m |r_m| |(Phi x)_m|, amplified by 1/h in the difference
+    # (measured 0.7% of the largest gradient entry here); the FP32 gradient itself was
+    # checked against the FP64 oracle gradient above at 1e-5.
+    tol = 1e-6 if precision == "f64" else 2e-2
     assert np.max(np.abs(fd - g.ravel()[pix])) <= tol * np.max(np.abs(g))
 
 
