@@ -278,10 +278,12 @@ template <typename R> static PassCfg pass_cfg(const pd_plan* p) {
     constexpr int E = FftE<R>::value;
     const int nx = p->g.nx, ny = p->g.ny;
     PassCfg c{};
+    // at most 100 KB of shared memory and 512 threads per CTA, so two CTAs share an SM
+    // and one CTA's loads overlap the other's butterflies
     int rb = 4;
-    while (rb > 1 && (nx * 2 * rb / E > 1024 || (size_t)nx * 2 * rb * sizeof(cplx_t<R>) > 200 * 1024)) rb >>= 1;
+    while (rb > 1 && (nx * 2 * rb / E > 512 || (size_t)nx * 2 * rb * sizeof(cplx_t<R>) > 100 * 1024)) rb >>= 1;
     int cq = 4;
-    while (cq > 1 && (ny * 2 * cq / E > 1024 || (size_t)ny * 2 * cq * sizeof(cplx_t<R>) > 200 * 1024)) cq >>= 1;
+    while (cq > 1 && (ny * 2 * cq / E > 512 || (size_t)ny * 2 * cq * sizeof(cplx_t<R>) > 100 * 1024)) cq >>= 1;
     if (rb > ny) rb = ny;
     c.rows_per_cta = rb;
     c.cols_per_cta = cq;

@@ -193,22 +193,27 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
     }
 }
 
-// Per-block FP64 norms summed over the block's segments in a fixed order, the ball
-// scale c_i = max(0, 1 - eps_i/||r_i||) of step 8 (so v_new = c_i r_i = z - P_B(z)),
-// and the residual norm ||G_i b - y_i|| for the adaptive probabilities of Sec. 4.
+// Per-block FP64 norms summed over the block's segments in a fixed order (one warp per
+// block: lane-strided partial sums, then a fixed shuffle tree), the ball scale
+// c_i = max(0, 1 - eps_i/||r_i||) of step 8 (so v_new = c_i r_i = z - P_B(z)), and the
+// residual norm ||G_i b - y_i|| for the adaptive probabilities of Sec. 4.
 template <typename R>
 __global__ void k_block_norms(const double* __restrict__ part, const int32_t* __restrict__ bss,
                               const int32_t* __restrict__ bsl, const int32_t* __restrict__ active,
                               const double* __restrict__ eps, double* __restrict__ bnorm, R* __restrict__ scale,
                               double* __restrict__ res_norm, int d) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d || !active[i]) return;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= d || !active[i]) return;     // whole warps leave together
     double sr = 0.0, sd = 0.0;
-    for (int k = bss[i]; k < bss[i + 1]; ++k) {
+    for (int k = bss[i] + lane; k < bss[i + 1]; k += 32) {
         const int sg = bsl[k];
         sr += part[2 * sg];
         sd += part[2 * sg + 1];
     }
+    sr = warp_sum(sr);
+    sd = warp_sum(sd);
+    if (lane != 0) return;
     bnorm[2 * i] = sr;
     bnorm[2 * i + 1] = sd;
     const double nr = sqrt(sr);
@@ -442,12 +447,15 @@ __global__ void __launch_bounds__(256) k_grid8c(const cplx_t<R>* __restrict__ sr
     }
 }
 
-// Add the neighbours' halo rings to each tile's border cells (periodic grid).
+// Add the neighbours' halo rings to each tile's border cells (periodic grid). Only the
+// cells within A = J/2 of the tile's start or H = J/2 - 1 of its end can receive ring
+// contributions: A*T + H*T cells in full rows plus (A + H) cells in each middle row.
 template <typename R>
 __global__ void __launch_bounds__(256) k_halo_merge(cplx_t<R>* __restrict__ U, const cplx_t<R>* __restrict__ ring,
                                                     const int32_t* __restrict__ flag, Geo g) {
     using C2 = cplx_t<R>;
     const int H = g.halo_lo, A = g.halo_hi, T = g.tile, E = g.ext;
+    const int nborder = (A + H) * T + (T - A - H) * (A + H);
     for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
         int nb[9];
@@ -460,9 +468,16 @@ __global__ void __launch_bounds__(256) k_halo_merge(cplx_t<R>* __restrict__ U, c
             if (k != 4 && flag[nb[k]]) any = true;
         }
         if (!any) continue;
-        for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-            const int iy = i / T, ix = i - iy * T;
-            if (iy >= A && iy < T - H && ix >= A && ix < T - H) continue;
+        for (int i = threadIdx.x; i < nborder; i += blockDim.x) {
+            int iy, ix;
+            if (i < A * T) { iy = i / T; ix = i - iy * T; }
+            else if (i < (A + H) * T) { const int k = i - A * T; iy = T - H + k / T; ix = k - (k / T) * T; }
+            else {
+                const int k = i - (A + H) * T, w = A + H;
+                iy = A + k / w;
+                const int c = k - (k / w) * w;
+                ix = c < A ? c : T - H + (c - A);
+            }
             C2 sum = mk<C2>(R(0), R(0));
             bool hit = false;
 #pragma unroll
@@ -533,7 +548,7 @@ cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs&
     prof_mark(PH_DEGRID, 1, s);
     if (e) return e;
     prof_mark(PH_NORMS, 0, s);
-    k_block_norms<R><<<(p->d + 127) / 128, 128, 0, s>>>(p->seg_part, p->block_seg_start, p->block_seg_list,
+    k_block_norms<R><<<(p->d * 32 + 127) / 128, 128, 0, s>>>(p->seg_part, p->block_seg_start, p->block_seg_list,
                                                        a.block_active, a.eps, p->blk_norm, (R*)p->blk_scale,
                                                        a.res_norm, p->d);
     prof_mark(PH_NORMS, 1, s);
