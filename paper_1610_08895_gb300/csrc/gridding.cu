@@ -29,17 +29,22 @@ namespace pdgb {
 
 // The J tap weights phi(frac + J/2 - 1 - a) of one axis. FP32: the plan's per-tap
 // Chebyshev interpolants (degree 10, interpolation error ~3e-11 of phi(0), below FP32
-// resolution) evaluated by Horner in x = 2 frac - 1. FP64: I0 itself.
+// resolution) in x = 2 frac - 1. phi is even, so tap J-1-a is tap a at -x: with the
+// polynomial split into even and odd parts p = E(x^2) + x O(x^2), one pass gives both
+// E + x O (tap a) and E - x O (tap J-1-a). FP64: I0 itself.
 template <typename R, int J>
 __device__ __forceinline__ void kb_taps(R frac, R* w, R two_over_j, R beta, const KbPoly& kp) {
     if constexpr (sizeof(R) == 4) {
-        const float x = 2.0f * frac - 1.0f;
+        const float x = 2.0f * frac - 1.0f, x2 = x * x;
 #pragma unroll
-        for (int a = 0; a < J; ++a) {
-            float acc = kp.c[a][KB_DEG];
+        for (int a = 0; a < J / 2; ++a) {
+            float ev = kp.c[a][KB_DEG], od = kp.c[a][KB_DEG - 1];
 #pragma unroll
-            for (int k = KB_DEG - 1; k >= 0; --k) acc = fmaf(acc, x, kp.c[a][k]);
-            w[a] = acc;
+            for (int k = KB_DEG - 2; k >= 0; k -= 2) ev = fmaf(ev, x2, kp.c[a][k]);
+#pragma unroll
+            for (int k = KB_DEG - 3; k >= 1; k -= 2) od = fmaf(od, x2, kp.c[a][k]);
+            w[a] = fmaf(x, od, ev);
+            w[J - 1 - a] = fmaf(-x, od, ev);
         }
     } else {
 #pragma unroll
@@ -328,10 +333,11 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
 // phases (row parity, column parity); in a phase the footprints of different
 // super-cells are disjoint, so each warp owns one super-cell at a time. Lane l owns
 // the cells whose (row mod 8, column mod 8) is (l / 4, 2 (l % 4) + {0, 1}): every
-// footprint holds exactly one cell of each class, so a lane updates its two cells of
-// each visibility with plain shared-memory read-modify-writes and no other lane ever
-// touches them. Each warp first stages 32 visibilities (weights, value, cell), one
-// per lane.
+// footprint holds exactly one cell of each class, so no other lane ever touches them.
+// A lane keeps the running sum of its current cell of each class in registers and
+// adds it to the shared accumulator (plain read-modify-write) only when the cell
+// changes; in the row-major order of a super-cell that is about once per 8 cells of
+// travel. Each warp first stages 32 visibilities (weights, value, cell), one per lane.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(256) k_grid8c(const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf,
                                                 cplx_t<R>* __restrict__ v, const R* __restrict__ scale,
@@ -381,6 +387,9 @@ __global__ void __launch_bounds__(256) k_grid8c(const cplx_t<R>* __restrict__ sr
                 if (k >= hy * hx) break;
                 const int sc = (2 * (k / hx) + py) * nsc_side + 2 * (k % hx) + px;
                 int fill = 0;
+                // running sums of this lane's two cells (classes (lcy, lcx), (lcy, lcx + 1))
+                int key0 = -1, key1 = -1;
+                C2 r0 = mk<C2>(R(0), R(0)), r1 = mk<C2>(R(0), R(0));
                 for (int j = 0; j <= nact; ++j) {
                     int pos = 0, end = 0;
                     R scv = R(0);
@@ -411,20 +420,30 @@ __global__ void __launch_bounds__(256) k_grid8c(const cplx_t<R>* __restrict__ sr
                             const int bx = c & 0xFFFF, by = c >> 16;
                             const int b = (lcy - by + 3) & 7;
                             const int a0 = (lcx - bx + 3) & 7, a1 = (lcx + 1 - bx + 3) & 7;
+                            const int rowk = (by - oy + b) * E + (bx - ox);
+                            const int k0 = rowk + a0, k1 = rowk + a1;
+                            if (k0 != key0) {
+                                if (key0 >= 0) { C2 t0 = acc[key0]; t0.x += r0.x; t0.y += r0.y; acc[key0] = t0; }
+                                key0 = k0;
+                                r0 = mk<C2>(R(0), R(0));
+                            }
+                            if (k1 != key1) {
+                                if (key1 >= 0) { C2 t1 = acc[key1]; t1.x += r1.x; t1.y += r1.y; acc[key1] = t1; }
+                                key1 = k1;
+                                r1 = mk<C2>(R(0), R(0));
+                            }
                             const R wy = sw[warp][q][J + b];
                             const R w0 = sw[warp][q][a0] * wy, w1 = sw[warp][q][a1] * wy;
                             const C2 d = sd[warp][q];
-                            C2* row = acc + (by - oy + b) * E + (bx - ox);
-                            C2 v0 = row[a0], v1 = row[a1];
-                            v0.x += w0 * d.x; v0.y += w0 * d.y;
-                            v1.x += w1 * d.x; v1.y += w1 * d.y;
-                            row[a0] = v0;
-                            row[a1] = v1;
+                            r0.x += w0 * d.x; r0.y += w0 * d.y;
+                            r1.x += w1 * d.x; r1.y += w1 * d.y;
                         }
                         __syncwarp();
                         fill = 0;
                     }
                 }
+                if (key0 >= 0) { C2 t0 = acc[key0]; t0.x += r0.x; t0.y += r0.y; acc[key0] = t0; }
+                if (key1 >= 0) { C2 t1 = acc[key1]; t1.x += r1.x; t1.y += r1.y; acc[key1] = t1; }
             }
             __syncthreads();
         }
