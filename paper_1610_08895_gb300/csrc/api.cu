@@ -515,6 +515,9 @@ extern "C" pd_status pd_state_destroy(pd_state* st) {
     if (st->ev_in) cudaEventDestroy(st->ev_in);
     if (st->ev_out) cudaEventDestroy(st->ev_out);
     if (st->gstream) cudaStreamDestroy(st->gstream);
+    if (st->ev_fork) cudaEventDestroy(st->ev_fork);
+    if (st->ev_join) cudaEventDestroy(st->ev_join);
+    if (st->pstream) cudaStreamDestroy(st->pstream);
     for (cudaEvent_t e : st->prof_ev)
         if (e) cudaEventDestroy(e);
     free_all(st->allocs);
@@ -581,18 +584,42 @@ extern "C" pd_status pd_state_set_data(pd_plan* p, pd_state* st, const void* y, 
     return PD_OK;
 }
 
+// One iteration of Algorithm 1 on stream s. With `concurrent`, the sparsity-prior
+// branch (steps 13-14: reads x~, writes s, s~ and the plan's wavelet scratch) runs on the
+// state's second stream between a fork after the draws and a join before the primal
+// update, alongside the data-fidelity branch (steps 4-11: FFT, degridding, gridding),
+// as step 6 of the algorithm runs its blocks concurrently. Profiled iterations stay on
+// one stream so that each kernel phase is timed alone.
+static cudaError_t ensure_prior_stream(pd_state* st) {
+    if (st->pstream) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&st->pstream, cudaStreamNonBlocking))) return e;
+    if ((e = cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming))) return e;
+    return cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming);
+}
+
 template <typename R>
-static cudaError_t enqueue_iteration(pd_plan* p, pd_state* st, const pd_params* prm, cudaStream_t s) {
+static cudaError_t enqueue_iteration(pd_plan* p, pd_state* st, const pd_params* prm, cudaStream_t s,
+                                     bool concurrent = true) {
     cudaError_t e;
     SelectArgs sa{prm->seed, prm->adaptive, prm->adapt_n, prm->adapt_p_min, prm->adapt_p_max};
     if ((e = select_active(p, st, sa, s))) return e;
+    cudaStream_t ps = s;
+    if (concurrent) {
+        if ((e = ensure_prior_stream(st))) return e;
+        ps = st->pstream;
+        if ((e = cudaEventRecord(st->ev_fork, s))) return e;
+        if ((e = cudaStreamWaitEvent(ps, st->ev_fork, 0))) return e;
+    }
+    if ((e = sparsity_dual<R>(p, (const R*)st->xt, (R*)st->s, (R*)st->st, st->basis_active,
+                              prm->kappa * prm->psi_norm, ps)))
+        return e;
+    if (concurrent && (e = cudaEventRecord(st->ev_join, ps))) return e;
     if ((e = fwd_fft<R>(p, (const R*)st->xt, (cplx_t<R>*)p->gridb, s))) return e;
     DualArgs da{st->y, st->v, st->block_active, st->eps, st->res_norm};
     if ((e = degrid_dual<R>(p, (const cplx_t<R>*)p->gridb, da, st->act_tiles, st->counts, s))) return e;
     if ((e = grid_dual<R>(p, da, st->act_tiles, st->counts, st->tile_active, (cplx_t<R>*)st->u, s))) return e;
-    if ((e = sparsity_dual<R>(p, (const R*)st->xt, (R*)st->s, (R*)st->st, st->basis_active,
-                              prm->kappa * prm->psi_norm, s)))
-        return e;
+    if (concurrent && (e = cudaStreamWaitEvent(s, st->ev_join, 0))) return e;
     PrimalArgs pa{prm->tau, prm->sigma, prm->varsigma, st->x, st->xt, st->st, st->prim_part};
     if ((e = inv_fft<R>(p, (const cplx_t<R>*)st->u, nullptr, &pa, s))) return e;
     return primal_finish(p, st, s);
@@ -667,8 +694,8 @@ extern "C" pd_status pd_iterate(pd_plan* p, pd_state* st, const pd_params* prm, 
         for (int k = 0; k < niter; ++k) {
             for (cudaEvent_t e : st->prof_ev) CU(cudaEventRecord(e, s));   // phases not run read 0 ms
             g_prof = st;
-            cudaError_t e = p->prec == PD_F64 ? enqueue_iteration<double>(p, st, prm, s)
-                                              : enqueue_iteration<float>(p, st, prm, s);
+            cudaError_t e = p->prec == PD_F64 ? enqueue_iteration<double>(p, st, prm, s, false)
+                                              : enqueue_iteration<float>(p, st, prm, s, false);
             g_prof = nullptr;
             CU(e);
             CU(cudaStreamSynchronize(s));

@@ -140,6 +140,10 @@ struct pd_state {
     std::vector<unsigned char> gkey;
     cudaStream_t gstream = nullptr;    // private stream the graph is captured on and replayed on
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // second stream for the sparsity-prior branch of an iteration (Alg. 1 steps 12-15
+    // run concurrently with the data-fidelity steps 6-11), with its fork/join events
+    cudaStream_t pstream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // per-phase timing (pd_params.profile)
     cudaEvent_t prof_ev[2 * 12] = {};
     double prof_ms[12] = {};
