@@ -97,6 +97,19 @@ typedef struct {
  * Errors: PD_EINVAL (bad description), PD_ENOMEM, PD_ECUDA.
  */
 pd_status pd_plan_create(const pd_plan_desc* desc, pd_plan** out);
+
+/*
+ * Autotuner of the gridding tile edge (the tile and bin size of the tile-binned
+ * degridding and gridding). For each candidate tile (powers of two >= J) it builds
+ * the plan of `desc` with that tile, runs `iters` iterations of Algorithm 1 (after
+ * one warm-up) with every block and basis drawn at probability 1/2 on zero data,
+ * and times them with CUDA events on `stream`. Host outputs: the fastest tile in
+ * *best_tile and, if ms is non-NULL, the mean milliseconds per iteration of each
+ * candidate (ms[k] < 0 for a candidate the plan rejects). Allocates and frees the
+ * trial plans; synchronises `stream`. Use the result as desc->tile.
+ */
+pd_status pd_plan_autotune(const pd_plan_desc* desc, const int32_t* candidates, int32_t ncand, int32_t iters,
+                           int32_t* best_tile, double* ms, void* stream);
 pd_status pd_plan_destroy(pd_plan* plan);
 
 /* Static description of the last error on the calling thread (never NULL). */

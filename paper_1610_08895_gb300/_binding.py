@@ -47,6 +47,8 @@ _VP = ctypes.c_void_p
 _SIGS = {
     "pd_plan_create": ([ctypes.POINTER(PdPlanDesc), ctypes.POINTER(_VP)], ctypes.c_int),
     "pd_plan_destroy": ([_VP], ctypes.c_int),
+    "pd_plan_autotune": ([ctypes.POINTER(PdPlanDesc), _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP],
+                         ctypes.c_int),
     "pd_last_error": ([], ctypes.c_char_p),
     "pd_plan_info": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "pd_daubechies_filter": ([ctypes.c_int32, _VP], ctypes.c_int),

@@ -236,6 +236,26 @@ class State:
         B.call("pd_state_load", self.plan.handle, self._h, buf.ctypes.data, _stream())
 
 
+def autotune_tile(nx, ny, uv, block_of_vis, nblocks, kernel_width=8, basis_ids=(0,), levels=1, precision="f32",
+                  candidates=(16, 32, 64), iters=5):
+    """pd_plan_autotune: time Algorithm 1 iterations with each candidate gridding tile
+    and return (best tile, {tile: ms per iteration})."""
+    B.load()
+    uv = np.ascontiguousarray(uv, dtype=np.float64)
+    blk = np.ascontiguousarray(block_of_vis, dtype=np.int32)
+    ids = np.ascontiguousarray(basis_ids, dtype=np.int32)
+    prec = {"f32": B.PD_F32, "f64": B.PD_F64}[precision] if isinstance(precision, str) else int(precision)
+    d = B.PdPlanDesc(nx=int(nx), ny=int(ny), osf=2, nvis=len(uv), uv=uv.ctypes.data, nblocks=int(nblocks),
+                     block_of_vis=blk.ctypes.data, kernel_width=int(kernel_width), kb_beta=0.0, nbases=len(ids),
+                     basis_ids=ids.ctypes.data, levels=int(levels), precision=prec, tile=0)
+    cand = np.ascontiguousarray(candidates, dtype=np.int32)
+    ms = np.zeros(len(cand))
+    best = ctypes.c_int32()
+    B.call("pd_plan_autotune", ctypes.byref(d), cand.ctypes.data, len(cand), int(iters), ctypes.byref(best),
+           ms.ctypes.data, _stream())
+    return best.value, {int(c): float(t) for c, t in zip(cand, ms)}
+
+
 def psi_adj_noalloc(x, basis_ids, levels, coeffs=None):
     """Psi^H x through pd_apply_psi_adj_noalloc: no plan, no device allocation by the
     library (coeffs must be passed in by callers that cannot allocate)."""

@@ -811,3 +811,49 @@ extern "C" pd_status pd_state_load(const pd_plan* p, pd_state* st, const void* b
     CU(cudaStreamSynchronize(s));
     return PD_OK;
 }
+
+extern "C" pd_status pd_plan_autotune(const pd_plan_desc* desc, const int32_t* candidates, int32_t ncand,
+                                      int32_t iters, int32_t* best_tile, double* ms, void* stream) {
+    if (!desc || !candidates || ncand < 1 || iters < 1 || !best_tile)
+        return fail(PD_EINVAL, "pd_plan_autotune: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double best = -1.0;
+    *best_tile = 0;
+    for (int k = 0; k < ncand; ++k) {
+        if (ms) ms[k] = -1.0;
+        pd_plan_desc d = *desc;
+        d.tile = candidates[k];
+        pd_plan* p = nullptr;
+        if (pd_plan_create(&d, &p) != PD_OK) continue;
+        pd_state* st = nullptr;
+        pd_status rc = pd_state_create(p, &st);
+        void* y = nullptr;
+        if (rc == PD_OK && cudaMalloc(&y, (size_t)p->M * p->csz) != cudaSuccess) rc = PD_ENOMEM;
+        double t_ms = -1.0;
+        if (rc == PD_OK) {
+            cudaMemsetAsync(y, 0, (size_t)p->M * p->csz, s);
+            std::vector<double> eps(p->d, 1.0), pb(p->d, 0.5), pbs(p->b, 0.5);
+            pd_params prm{};
+            prm.tau = 0.49; prm.sigma = 1.0; prm.varsigma = 1e-3; prm.kappa = 1e-3; prm.psi_norm = 1.0;
+            prm.seed = 1; prm.p_block = pb.data(); prm.p_basis = pbs.data(); prm.use_graph = 1;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (pd_state_set_data(p, st, y, eps.data(), stream) == PD_OK &&
+                pd_iterate(p, st, &prm, 1, stream) == PD_OK && cudaEventCreate(&e0) == cudaSuccess &&
+                cudaEventCreate(&e1) == cudaSuccess && cudaEventRecord(e0, s) == cudaSuccess &&
+                pd_iterate(p, st, &prm, iters, stream) == PD_OK && cudaEventRecord(e1, s) == cudaSuccess &&
+                cudaEventSynchronize(e1) == cudaSuccess) {
+                float f = 0.f;
+                if (cudaEventElapsedTime(&f, e0, e1) == cudaSuccess) t_ms = f / iters;
+            }
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+        if (y) cudaFree(y);
+        pd_state_destroy(st);
+        pd_plan_destroy(p);
+        if (ms) ms[k] = t_ms;
+        if (t_ms > 0 && (best < 0 || t_ms < best)) { best = t_ms; *best_tile = candidates[k]; }
+    }
+    if (*best_tile == 0) return fail(PD_EINVAL, "pd_plan_autotune: no candidate tile could be planned and run");
+    return PD_OK;
+}

@@ -113,3 +113,13 @@ def test_draws_match_oracle_philox_every_iteration():
         rep = st.report()
         assert list(rep["block_active"]) == PH.active_set(11, t, 0, pb)
         assert list(rep["basis_active"]) == PH.active_set(11, t, 1, ps)
+
+
+def test_tile_autotuner_picks_a_working_tile():
+    from paper_1610_08895_gb300.api import autotune_tile
+    prob, _ = make_problem(128, 30000, 16, 8, (0, 1, 2), 3, uv_kind="radial", blocks="annuli", nannuli=16)
+    g = prob.geom
+    best, times = autotune_tile(g.nx, g.ny, prob.uv, prob.block_of_vis, prob.nblocks, kernel_width=8,
+                                basis_ids=prob.basis_ids, levels=prob.levels, candidates=(4, 16, 32, 64), iters=3)
+    assert times[4] < 0                      # below the kernel width: rejected by the plan
+    assert best in (16, 32, 64) and times[best] == min(t for t in times.values() if t > 0)
