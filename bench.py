@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--no-operators", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
@@ -150,6 +151,51 @@ def algorithmic_bytes(cfg, plan_info, m_active, tiles_active_frac, bases_active,
     }
 
 
+def _time_ms(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_operators(peak, stream, reps=20):
+    """Phi and Phi^H alone on a batch of 8 images: 1024^2 image, 2048^2 grid,
+    M = 4,194,304 Gaussian uv points, J = 8, FP32. Algorithmic bytes per image are the
+    sums of the per-pass figures: 100 N + 24 M for either operator (N pixels, M points)."""
+    import torch
+    from paper_1610_08895_gb300 import synth
+    from paper_1610_08895_gb300.api import Plan
+    n, m, batch = 1024, 4_194_304, 8
+    plan = Plan(n, n, synth.uv_gaussian(m, seed=31), np.zeros(m, np.int32), 1, kernel_width=8, precision="f32")
+    x = torch.tensor(synth.random_images(batch, n, n, seed=4), dtype=torch.float32, device="cuda")
+    y = torch.empty((batch, m), dtype=torch.complex64, device="cuda")
+    xa = torch.empty_like(x)
+    ms_phi = _time_ms(lambda: plan.pd_apply_phi(x, y), reps, stream)
+    ms_adj = _time_ms(lambda: plan.pd_apply_phi_adj(y, xa), reps, stream)
+    alg = (100.0 * n * n + 24.0 * m) * batch
+    plan.close()
+    out = {"workload": f"{n}x{n} image, {2 * n}x{2 * n} grid, M={m} Gaussian uv, J=8, batch {batch}, f32"}
+    for name, ms in (("phi", ms_phi), ("phi_adj", ms_adj)):
+        gbs = alg / (ms / 1e3) / 1e9
+        out[name] = {"ms_per_batch": round(ms, 4), "GBps": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    return out
+
+
+def run_cufft(n, stream, reps=20):
+    """cuFFT (torch.fft) 2-D transforms of one full (2n)^2 complex64 grid: the library
+    counterpart of the FFT passes (which skip the zero rows of Z and the cropped rows)."""
+    import torch
+    g = torch.randn((2 * n, 2 * n), dtype=torch.complex64, device="cuda")
+    return {"grid": f"{2 * n}x{2 * n} c64", "fft2_ms": round(_time_ms(lambda: torch.fft.fft2(g), reps, stream), 4),
+            "ifft2_ms": round(_time_ms(lambda: torch.fft.ifft2(g), reps, stream), 4)}
+
+
 KERNELS_PER_ITER = lambda L: 1 + 2 + 2 + 2 + (1 + L) + (L - 1 + 1) + 2 + 1   # noqa: E731
 
 
@@ -245,6 +291,15 @@ def run_ours(args):
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                 "traffic": None, "algorithmic_bytes_per_launch": int(alg[dom])}
 
+    # ---- Phi / Phi^H alone, and cuFFT as a timed comparison of the FFT passes
+    operators = None
+    if not args.no_operators:
+        operators = run_operators(peak, stream)
+        cf = run_cufft(n, stream)
+        cf["ours_forward_ms"] = round(kernels["fwd_rows"]["ms"] + kernels["fwd_cols"]["ms"], 4)
+        cf["ours_inverse_ms"] = round(kernels["inv_cols"]["ms"] + kernels["inv_rows_primal"]["ms"], 4)
+        operators["cufft_vs_fft_passes"] = cf
+
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -309,7 +364,7 @@ def run_ours(args):
                        "graph": "one CUDA graph per iteration, replayed", "setup_s": round(setup_s, 1),
                        "plan": info},
             "roofline": roofline, "kernels": kernels, "clocks": clk.summary(), "e2e": e2e,
-            "fp64": fp64, "cpu_baseline": cpu,
+            "fp64": fp64, "operators": operators, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

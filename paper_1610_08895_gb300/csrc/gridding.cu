@@ -87,16 +87,19 @@ __device__ __forceinline__ void list_active_segments(int seg0, int nseg_t, const
 
 // ---------------------------------------------------------------- degridding
 // Warp-level segmented sum: the lanes with ok add (a, b) to their local segment ls;
-// lane 0 adds each segment's warp total into part[2 ls], part[2 ls + 1] (slots owned
-// by this warp), always in the same order.
-__device__ __forceinline__ void warp_seg_add(bool ok, int ls, double a, double b, double* part) {
+// lane 0 adds each segment's warp total into part[2 ls], part[2 ls + 1] (FP64 slots
+// owned by this warp), always in the same order. The at most 32 terms of one warp are
+// summed in the working precision A (a fixed shuffle tree of non-negative terms:
+// relative error below 6 units of A's rounding), every sum above that in FP64.
+template <typename A>
+__device__ __forceinline__ void warp_seg_add(bool ok, int ls, A a, A b, double* part) {
     unsigned todo = __ballot_sync(0xffffffffu, ok);
     while (todo) {
         const int key = __shfl_sync(0xffffffffu, ls, __ffs(todo) - 1);
         const bool mine = ok && ls == key;
         const unsigned mask = __ballot_sync(0xffffffffu, mine);
-        const double x = warp_sum(mine ? a : 0.0), y = warp_sum(mine ? b : 0.0);
-        if ((threadIdx.x & 31) == 0) { part[2 * key] += x; part[2 * key + 1] += y; }
+        const A x = warp_sum(mine ? a : A(0)), y = warp_sum(mine ? b : A(0));
+        if ((threadIdx.x & 31) == 0) { part[2 * key] += (double)x; part[2 * key + 1] += (double)y; }
         todo &= ~mask;
     }
 }
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
         for (int base = 0; base < total; base += blockDim.x) {
             const int pos = base + threadIdx.x;
             const bool ok = pos < total;
-            double ar = 0.0, ad = 0.0;
+            R ar = R(0), ad = R(0);     // squares in the working precision (exact for FP64)
             if (ok) {
                 while (act_pre[j + 1] <= pos) ++j;
                 const int m = seg_start[act_seg[j]] + pos - act_pre[j];
@@ -176,8 +179,8 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                     const R dx = sx - yy.x, dy = sy - yy.y;
                     const C2 r = mk<C2>(vv.x + dx, vv.y + dy);
                     rbuf[m] = r;
-                    ar = (double)r.x * r.x + (double)r.y * r.y;
-                    ad = (double)dx * dx + (double)dy * dy;
+                    ar = r.x * r.x + r.y * r.y;
+                    ad = dx * dx + dy * dy;
                 }
             }
             if (MODE == 1) warp_seg_add(ok, j, ar, ad, mypart);
