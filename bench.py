@@ -131,6 +131,25 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def job_throughput(ms_local, steps, device="cuda"):
+    """Max over ranks of the timed region (ms) and the whole-job throughput. Every rank
+    solves its own problem (weak scaling), so value = world * steps / max time."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = float(ms_local)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms / 1e3)
+
+
+def rank_seed(seed, rank):
+    """Data seed of a rank's independent problem."""
+    return seed + 100 * rank
+
+
 def algorithmic_bytes(cfg, plan_info, m_active, tiles_active_frac, bases_active, dirac_active):
     """Bytes each phase must move per launch (FP32): the reads and writes its result needs."""
     n = cfg["n"]
@@ -217,7 +236,7 @@ def run_ours(args):
     cfg = WORKLOADS[args.workload]
     n, m = cfg["n"], cfg["m"]
     t0 = time.time()
-    uv, blk, x_true, noise = make_inputs(cfg, args.seed + 100 * rank)
+    uv, blk, x_true, noise = make_inputs(cfg, rank_seed(args.seed, rank))
     d = int(blk.max()) + 1
     b = len(cfg["bases"])
     plan = Plan(n, n, uv, blk, d, kernel_width=cfg["J"], basis_ids=cfg["bases"], levels=cfg["levels"],
@@ -254,12 +273,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * args.steps / (ms / 1e3)
+    ms, value = job_throughput(e0.elapsed_time(e1), args.steps)
 
     # ---- per-kernel times (CUDA events on the launching stream) over K instrumented iterations
     st.profile(reset=True)

@@ -57,7 +57,8 @@ typedef struct pd_state pd_state;
 /*
  * Plan description (host memory, read only during pd_plan_create).
  *
- * nx, ny        image size; powers of two in [16, 8192].
+ * nx, ny        image size; powers of two in [16, 8192] (FP32) or [16, 4096] (FP64,
+ *               PD_ENOTSUP above: one FFT row of 8192 FP64 values needs 2048 threads).
  * osf           oversampling per axis; must be 2 (the paper's k = 4 total,
  *               Sec. 5 "oversampling ratio k=4"), giving a (2ny) x (2nx) grid.
  * nvis          number of visibilities M >= 1.

@@ -121,6 +121,8 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
     if (!is_pow2(d->nx) || !is_pow2(d->ny) || d->nx < 16 || d->ny < 16 || d->nx > 8192 || d->ny > 8192)
         return fail(PD_EINVAL, "image sides must be powers of two in [16, 8192]");
     if (d->osf != 2) return fail(PD_EINVAL, "oversampling per axis must be 2");
+    if (d->precision == PD_F64 && (d->nx > 4096 || d->ny > 4096))
+        return fail(PD_ENOTSUP, "FP64 plans support image sides up to 4096");
     if (d->nvis < 1 || d->nvis > (int64_t)0x7fffffff) return fail(PD_EINVAL, "nvis must be in [1, 2^31)");
     if (!d->uv || !d->block_of_vis) return fail(PD_EINVAL, "uv and block_of_vis must be non-null");
     if (d->nblocks < 1 || d->nblocks > 4096) return fail(PD_EINVAL, "nblocks must be in [1, 4096]");

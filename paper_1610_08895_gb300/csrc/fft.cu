@@ -67,12 +67,20 @@ template <int RAD> __host__ __device__ constexpr int bitrev(int k) {
 // memory through ld(l, c) (GIN), and the last can hand its outputs to st(k, c, value,
 // active) instead of shared memory (GOUT). st is called by every thread of the CTA, so
 // it may exchange values between the lanes of a warp.
+// threadIdx.x read through a volatile move, so the index arithmetic derived from it is
+// redone per stage instead of being hoisted and held in registers across stages.
+__device__ __forceinline__ int tid_here() {
+    int t;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
+    return t;
+}
+
 template <typename R, int E, int RAD, int SIGN, bool GIN, bool GOUT, class Ld, class St>
 __device__ __forceinline__ void stockham_stage(cplx_t<R>* s, int L, int logC, int Ns, const cplx_t<R>* tw2L,
                                                int nwork, const Ld& ld, const St& st) {
     using C2 = cplx_t<R>;
     constexpr int JOBS = E / RAD;
-    const int tid = threadIdx.x;
+    const int tid = tid_here();
     const bool act = tid < nwork;
     const int LR = L / RAD;
     const int Cm = (1 << logC) - 1;
@@ -118,18 +126,18 @@ __device__ __forceinline__ void stockham_stage(cplx_t<R>* s, int L, int logC, in
     if (!GOUT) __syncthreads();
 }
 
-template <typename R, int E, int RAD, int SIGN, bool GOUT, class Ld, class St>
+template <typename R, int E, int RAD, int SIGN, bool GIN, bool GOUT, class Ld, class St>
 __device__ __forceinline__ void first_stage(cplx_t<R>* s, int L, int logC, const cplx_t<R>* tw2L, int nwork,
                                             bool last, const Ld& ld, const St& st) {
-    if (GOUT && last) stockham_stage<R, E, RAD, SIGN, true, GOUT>(s, L, logC, 1, tw2L, nwork, ld, st);
-    else stockham_stage<R, E, RAD, SIGN, true, false>(s, L, logC, 1, tw2L, nwork, ld, st);
+    if (GOUT && last) stockham_stage<R, E, RAD, SIGN, GIN, GOUT>(s, L, logC, 1, tw2L, nwork, ld, st);
+    else stockham_stage<R, E, RAD, SIGN, GIN, false>(s, L, logC, 1, tw2L, nwork, ld, st);
 }
 
 // C = 2^logC independent length-L DFTs (SIGN -1 forward, +1 inverse, unnormalised)
-// with tw2L[k] = exp(-2 pi i k / (2L)). Inputs come from ld; outputs go to st when
-// GOUT, else they are left in natural order in s[k * C + c]. The odd-sized radix runs
-// first, where all its twiddles are 1.
-template <typename R, int E, int SIGN, bool GOUT, class Ld, class St>
+// with tw2L[k] = exp(-2 pi i k / (2L)). Inputs come from ld when GIN, else from s in
+// natural order s[l * C + c]; outputs go to st when GOUT, else they are left in natural
+// order in s. The odd-sized radix runs first, where all its twiddles are 1.
+template <typename R, int E, int SIGN, bool GIN, bool GOUT, class Ld, class St>
 __device__ void fft_io(cplx_t<R>* s, int L, int logC, const cplx_t<R>* tw2L, const Ld& ld, const St& st) {
     constexpr int LOGE = E >= 16 ? 4 : 3;
     constexpr int RB = 1 << LOGE;
@@ -138,10 +146,10 @@ __device__ void fft_io(cplx_t<R>* s, int L, int logC, const cplx_t<R>* tw2L, con
     const int rem = bits % LOGE;
     const int nst = bits / LOGE + (rem ? 1 : 0);
     const bool last = nst == 1;
-    if (rem == 3) first_stage<R, E, 8, SIGN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
-    else if (rem == 2) first_stage<R, E, 4, SIGN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
-    else if (rem == 1) first_stage<R, E, 2, SIGN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
-    else first_stage<R, E, RB, SIGN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
+    if (rem == 3) first_stage<R, E, 8, SIGN, GIN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
+    else if (rem == 2) first_stage<R, E, 4, SIGN, GIN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
+    else if (rem == 1) first_stage<R, E, 2, SIGN, GIN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
+    else first_stage<R, E, RB, SIGN, GIN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
     int Ns = rem ? 1 << rem : RB;
     for (int b = nst - 1; b > 0; --b) {
         if (GOUT && b == 1) stockham_stage<R, E, RB, SIGN, false, GOUT>(s, L, logC, Ns, tw2L, nwork, ld, st);
@@ -161,9 +169,8 @@ template <typename C> __device__ __forceinline__ C shfl_xor(C v, int m) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward row pass (Z then F along x): RB image rows per CTA. Sequence c = 2 rho + r
-// is image row iy0 + rho, deapodised and, for the odd outputs (r = 1), pre-twiddled;
-// its output k is kx = 2 k + r, stored straight into the column panels of t1.
+// Forward row pass (Z then F along x): RB image rows per CTA; smem column 2*rho + r
+// holds row rho pre-twiddled for the even (r = 0) or odd (r = 1) outputs.
 template <typename R>
 __global__ void __launch_bounds__(1024) k_fwd_rows(const R* __restrict__ x, cplx_t<R>* __restrict__ t1,
                                                    const R* __restrict__ cx, const R* __restrict__ cy,
@@ -171,53 +178,59 @@ __global__ void __launch_bounds__(1024) k_fwd_rows(const R* __restrict__ x, cplx
     using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* s = reinterpret_cast<C2*>(smraw);
-    const int logC = 31 - __clz(2 * RB);
-    const int Kx = 2 * nx, h = nx / 2;
+    const int logC = 31 - __clz(2 * RB), C = 2 * RB;
+    const int Kx = 2 * nx;
     const int iy0 = blockIdx.x * RB;
-    auto ld = [&](int m, int c) {
-        const int lc = m < h ? m : m - nx;            // centred column: m = lc mod nx
-        const int ix = lc + h, iy = iy0 + (c >> 1);
+    for (int e = threadIdx.x; e < RB * nx; e += blockDim.x) {
+        const int rho = e / nx, ix = e - rho * nx;
+        const int iy = iy0 + rho;
         const R val = x[(int64_t)iy * nx + ix] * cx[ix] * cy[iy];
-        C2 o = mk<C2>(val, R(0));
-        if (c & 1) {
-            const C2 w = twx[lc & (Kx - 1)];
-            o = mk<C2>(val * w.x, val * w.y);
-        }
-        return o;
-    };
-    auto st = [&](int k, int c, C2 v, bool act) {
-        if (!act) return;
-        const int kx = 2 * k + (c & 1);
-        t1[(((int64_t)(kx >> 2) * ny + iy0 + (c >> 1)) << 2) + (kx & 3)] = v;
-    };
-    fft_io<R, FftE<R>::value, -1, true>(s, nx, logC, twx, ld, st);
+        const int lc = ix - nx / 2;
+        const int m = lc & (nx - 1);
+        const C2 w = twx[lc & (Kx - 1)];
+        s[m * C + 2 * rho] = mk<C2>(val, R(0));
+        s[m * C + 2 * rho + 1] = mk<C2>(val * w.x, val * w.y);
+    }
+    __syncthreads();
+    auto nl = [](int, int) { return mk<C2>(R(0), R(0)); };
+    auto ns = [](int, int, C2, bool) {};
+    fft_io<R, FftE<R>::value, -1, false, false>(s, nx, logC, twx, nl, ns);
+    for (int e = threadIdx.x; e < RB * Kx; e += blockDim.x) {
+        const int p = e / (4 * RB), rem = e - p * 4 * RB;
+        const int rho = rem >> 2, q = rem & 3;
+        const int kx = 4 * p + q;
+        t1[((int64_t)p * ny + iy0 + rho) * 4 + q] = s[(kx >> 1) * C + 2 * rho + (kx & 1)];
+    }
 }
 
-// Forward column pass (F along y): CQ columns of one panel per CTA. Sequence
-// c = r CQ + qq is column q0 + qq, pre-twiddled for output parity r; output k of it is
-// row ky = 2 k + r of the grid panel.
+// Forward column pass (F along y): CQ columns of one panel per CTA; smem column
+// r * CQ + qq holds column qq pre-twiddled for output parity r.
 template <typename R>
 __global__ void __launch_bounds__(1024) k_fwd_cols(const cplx_t<R>* __restrict__ t1, cplx_t<R>* __restrict__ gb,
                                                    const cplx_t<R>* __restrict__ twy, int ny, int CQ) {
     using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* s = reinterpret_cast<C2*>(smraw);
-    const int C = 2 * CQ, logC = 31 - __clz(C), lq = logC - 1;
-    const int Ky = 2 * ny, h = ny / 2;
+    const int C = 2 * CQ, logC = 31 - __clz(C);
+    const int Ky = 2 * ny;
     const int per = 4 / CQ;
     const int p = blockIdx.x / per, q0 = (blockIdx.x - p * per) * CQ;
-    const C2* src = t1 + ((int64_t)p * ny << 2) + q0;
-    C2* dst = gb + ((int64_t)p * Ky << 2) + q0;
-    auto ld = [&](int m, int c) {
-        const int lc = m < h ? m : m - ny;
-        C2 val = src[((lc + h) << 2) + (c & (CQ - 1))];
-        if (c >> lq) val = cmul(val, twy[lc & (Ky - 1)]);
-        return val;
-    };
-    auto st = [&](int k, int c, C2 v, bool act) {
-        if (act) dst[((2 * k + (c >> lq)) << 2) + (c & (CQ - 1))] = v;
-    };
-    fft_io<R, FftE<R>::value, -1, true>(s, ny, logC, twy, ld, st);
+    for (int e = threadIdx.x; e < ny * CQ; e += blockDim.x) {
+        const int iy = e / CQ, qq = e - iy * CQ;
+        const C2 val = t1[((int64_t)p * ny + iy) * 4 + q0 + qq];
+        const int lc = iy - ny / 2;
+        const int m = lc & (ny - 1);
+        s[m * C + qq] = val;
+        s[m * C + CQ + qq] = cmul(val, twy[lc & (Ky - 1)]);
+    }
+    __syncthreads();
+    auto nl = [](int, int) { return mk<C2>(R(0), R(0)); };
+    auto ns = [](int, int, C2, bool) {};
+    fft_io<R, FftE<R>::value, -1, false, false>(s, ny, logC, twy, nl, ns);
+    for (int e = threadIdx.x; e < Ky * CQ; e += blockDim.x) {
+        const int ky = e / CQ, qq = e - ky * CQ;
+        gb[((int64_t)p * Ky + ky) * 4 + q0 + qq] = s[(ky >> 1) * C + (ky & 1) * CQ + qq];
+    }
 }
 
 // Inverse column pass (F^H along y, crop to ny rows). Sequence c = r CQ + qq holds the
@@ -245,10 +258,10 @@ __global__ void __launch_bounds__(1024) k_inv_cols(const cplx_t<R>* __restrict__
                 dst[((lc + h) << 2) + c] = cadd(v, cmul(cconj(twy[lc & (Ky - 1)]), o));
             }
         };
-        fft_io<R, FftE<R>::value, +1, true>(s, ny, logC, twy, ld, st);
+        fft_io<R, FftE<R>::value, +1, true, true>(s, ny, logC, twy, ld, st);
     } else {
         auto st = [](int, int, C2, bool) {};
-        fft_io<R, FftE<R>::value, +1, false>(s, ny, logC, twy, ld, st);
+        fft_io<R, FftE<R>::value, +1, true, false>(s, ny, logC, twy, ld, st);
         for (int e = threadIdx.x; e < ny * CQ; e += blockDim.x) {
             const int iy = e / CQ, qq = e - iy * CQ;
             const int lc = iy - h;
@@ -308,10 +321,10 @@ __global__ void __launch_bounds__(1024) k_inv_rows(const cplx_t<R>* __restrict__
                 finish(iy0 + (c >> 1), lc + h, v.x + (w.x * o.x - w.y * o.y));
             }
         };
-        fft_io<R, FftE<R>::value, +1, true>(s, nx, logC, twx, ld, st);
+        fft_io<R, FftE<R>::value, +1, true, true>(s, nx, logC, twx, ld, st);
     } else {
         auto st = [](int, int, C2, bool) {};
-        fft_io<R, FftE<R>::value, +1, false>(s, nx, logC, twx, ld, st);
+        fft_io<R, FftE<R>::value, +1, true, false>(s, nx, logC, twx, ld, st);
         for (int e = threadIdx.x; e < RB * nx; e += blockDim.x) {
             const int rho = e / nx, ix = e - rho * nx;
             const int lc = ix - h;

@@ -64,6 +64,26 @@ def test_phi_and_adjoint_match_oracle(case, precision):
 
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
+@pytest.mark.parametrize("nx,ny", [(64, 32), (32, 128), (16, 256)])
+def test_phi_rectangular_images(nx, ny, precision):
+    """Non-square images: the row and column passes see different lengths and panel counts."""
+    from paper_1610_08895_gb300.api import Plan
+    m = 3000
+    uv = synth.uv_gaussian(m, seed=13)
+    plan = Plan(nx, ny, uv, np.zeros(m, np.int32), 1, kernel_width=8, precision=precision)
+    geo = meas.Geometry(ny, nx, 8)
+    rng = np.random.default_rng(2)
+    x0 = rng.uniform(size=(ny, nx))
+    rdt = torch.float32 if precision == "f32" else torch.float64
+    y = plan.pd_apply_phi(torch.tensor(x0, dtype=rdt, device="cuda"))
+    tol = TOL_OP32 if precision == "f32" else TOL_OP64
+    assert rel(y.cpu().numpy(), geo.phi(x0, uv)) < tol
+    v = rng.normal(size=m) + 1j * rng.normal(size=m)
+    xa = plan.pd_apply_phi_adj(torch.tensor(v, dtype=plan.cplx_dtype, device="cuda"))
+    assert rel(xa.cpu().numpy(), geo.phi_adj(v, uv)) < tol
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_phi_batched_and_edge_points(precision):
     n = 32
     uv = np.concatenate([synth.uv_gaussian(500, seed=9),
