@@ -121,8 +121,13 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                                                 int max_segs, Geo g, R two_over_j, R beta, const KbPoly kp) {
     using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2* win = reinterpret_cast<C2*>(smraw);                              // [ext][ext]
-    double* part = reinterpret_cast<double*>(win + g.ext * g.ext);      // [8 warps][max_segs][2]
+    // FP32: the window twice, row stride EP (even), the second copy shifted left by one
+    // column, so every footprint row is J/2 aligned 16-byte pairs in one of the copies.
+    // FP64: one copy, row stride E.
+    constexpr bool PAIRS = sizeof(R) == 4;
+    const int EP = PAIRS ? ((g.ext + 2) & ~1) : g.ext;
+    C2* win = reinterpret_cast<C2*>(smraw);                              // [ext][EP] (x2 in FP32)
+    double* part = reinterpret_cast<double*>(win + (PAIRS ? 2 : 1) * g.ext * EP);  // [8 warps][max_segs][2]
     int* act_seg = reinterpret_cast<int*>(part + 16 * max_segs);        // [max_segs]
     int* act_pre = act_seg + max_segs;                                   // [max_segs + 1]
     __shared__ int nact_s;
@@ -139,7 +144,9 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
         for (int i = threadIdx.x; i < E * E; i += blockDim.x) {
             const int ey = i / E, ex = i - ey * E;
             const int ky = (oy - H + ey) & (g.Ky - 1), kx = (ox - H + ex) & (g.Kx - 1);
-            win[i] = grid[panel_off(ky, kx, g.Ky)];
+            const C2 gv = grid[panel_off(ky, kx, g.Ky)];
+            win[ey * EP + ex] = gv;
+            if (PAIRS && ex > 0) win[E * EP + ey * EP + ex - 1] = gv;
         }
         if (MODE == 1)
             for (int i = threadIdx.x; i < 16 * nseg_t; i += blockDim.x) part[i] = 0.0;
@@ -158,19 +165,37 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                 kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
                 kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
                 const int c = cell[m];
-                const C2* bp = win + ((c >> 16) - oy) * E + ((c & 0xFFFF) - ox);
+                const int r0 = (c >> 16) - oy, c0 = (c & 0xFFFF) - ox;   // footprint origin in the window
                 R sx = 0, sy = 0;
+                if constexpr (PAIRS) {
+                    const float4* bp = reinterpret_cast<const float4*>(
+                        (c0 & 1) ? win + E * EP + r0 * EP + c0 - 1 : win + r0 * EP + c0);
 #pragma unroll
-                for (int b = 0; b < J; ++b) {
-                    R rx = 0, ry = 0;
+                    for (int b = 0; b < J; ++b) {
+                        R rx = 0, ry = 0;
 #pragma unroll
-                    for (int a = 0; a < J; ++a) {
-                        const C2 gv = bp[b * E + a];
-                        rx += wx[a] * gv.x;
-                        ry += wx[a] * gv.y;
+                        for (int a = 0; a < J / 2; ++a) {
+                            const float4 q = bp[(b * EP >> 1) + a];
+                            rx += wx[2 * a] * q.x + wx[2 * a + 1] * q.z;
+                            ry += wx[2 * a] * q.y + wx[2 * a + 1] * q.w;
+                        }
+                        sx += wy[b] * rx;
+                        sy += wy[b] * ry;
                     }
-                    sx += wy[b] * rx;
-                    sy += wy[b] * ry;
+                } else {
+                    const C2* bp = win + r0 * EP + c0;
+#pragma unroll
+                    for (int b = 0; b < J; ++b) {
+                        R rx = 0, ry = 0;
+#pragma unroll
+                        for (int a = 0; a < J; ++a) {
+                            const C2 gv = bp[b * EP + a];
+                            rx += wx[a] * gv.x;
+                            ry += wx[a] * gv.y;
+                        }
+                        sx += wy[b] * rx;
+                        sy += wy[b] * ry;
+                    }
                 }
                 if (MODE == 0) {
                     out[perm[m]] = mk<C2>(sx, sy);
@@ -539,8 +564,8 @@ static cudaError_t launch_degrid(const pd_plan* p, const cplx_t<R>* grid, cplx_t
                                  const int32_t* tiles, const int32_t* count, int ctas, cudaStream_t s) {
     const Geo& g = p->g;
     const int ms = std::max(p->max_tile_segs, 1);
-    const size_t smem = (size_t)g.ext * g.ext * sizeof(cplx_t<R>) + (size_t)16 * ms * sizeof(double) +
-                        (size_t)(2 * ms + 1) * sizeof(int);
+    const size_t win = sizeof(R) == 4 ? (size_t)2 * g.ext * ((g.ext + 2) & ~1) : (size_t)g.ext * g.ext;
+    const size_t smem = win * sizeof(cplx_t<R>) + (size_t)16 * ms * sizeof(double) + (size_t)(2 * ms + 1) * sizeof(int);
     cudaError_t e = ensure_smem(k_degrid<R, J, MODE>, smem);
     if (e) return e;
     k_degrid<R, J, MODE><<<ctas, 256, smem, s>>>(
