@@ -365,7 +365,8 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
 // A lane keeps the running sum of its current cell of each class in registers and
 // adds it to the shared accumulator (plain read-modify-write) only when the cell
 // changes; in the row-major order of a super-cell that is about once per 8 cells of
-// travel. Each warp first stages 32 visibilities (weights, value, cell), one per lane.
+// travel. Each warp first stages 32 visibilities (weights, value, footprint origin in
+// the window with the base cell's row and column mod 8), one per lane.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(256) k_grid8c(const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf,
                                                 cplx_t<R>* __restrict__ v, const R* __restrict__ scale,
@@ -438,17 +439,19 @@ __global__ void __launch_bounds__(256) k_grid8c(const cplx_t<R>* __restrict__ sr
 #pragma unroll
                             for (int a = 0; a < J; ++a) { sw[warp][lane][a] = wx[a]; sw[warp][lane][J + a] = wy[a]; }
                             sd[warp][lane] = grid_value<R, MODE>(m, src, rbuf, v, perm, scv);
-                            scl[warp][lane] = cell[m];
+                            const int c = cell[m];
+                            const int bx = c & 0xFFFF, by = c >> 16;
+                            // footprint origin in the window, and the base cell's row and column mod 8
+                            scl[warp][lane] = (((by - oy) * E + (bx - ox)) << 6) | ((by & 7) << 3) | (bx & 7);
                         }
                         if (take > 0) { fill += take; pos += take; }
                         if (fill < 32 && j < nact) break;
                         __syncwarp();
                         for (int q = 0; q < fill; ++q) {
-                            const int c = scl[warp][q];
-                            const int bx = c & 0xFFFF, by = c >> 16;
-                            const int b = (lcy - by + 3) & 7;
-                            const int a0 = (lcx - bx + 3) & 7, a1 = (lcx + 1 - bx + 3) & 7;
-                            const int rowk = (by - oy + b) * E + (bx - ox);
+                            const int pk = scl[warp][q];
+                            const int b = (lcy - ((pk >> 3) & 7) + 3) & 7;
+                            const int a0 = (lcx - (pk & 7) + 3) & 7, a1 = (a0 + 1) & 7;
+                            const int rowk = (pk >> 6) + b * E;
                             const int k0 = rowk + a0, k1 = rowk + a1;
                             if (k0 != key0) {
                                 if (key0 >= 0) { C2 t0 = acc[key0]; t0.x += r0.x; t0.y += r0.y; acc[key0] = t0; }
