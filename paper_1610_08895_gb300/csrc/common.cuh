@@ -87,6 +87,26 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
+// dst[i] = load(i) for i < n over the CTA, with U independent global loads in flight per
+// thread: the plain strided loop waits for each load before issuing the next, which
+// leaves small grids bound by one memory latency per element a thread stages.
+template <int U, typename T, class F>
+__device__ __forceinline__ void stage_batched(T* dst, int n, const F& load) {
+    for (int base = threadIdx.x; base < n; base += U * (int)blockDim.x) {
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = base + u * (int)blockDim.x;
+            if (i < n) v[u] = load(i);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = base + u * (int)blockDim.x;
+            if (i < n) dst[i] = v[u];
+        }
+    }
+}
+
 // Allow a kernel `bytes` of dynamic shared memory. Static plus dynamic shared memory
 // above 48 KB needs the opt-in attribute, so it is always set to the requested size.
 template <typename K> inline cudaError_t ensure_smem(K kernel, size_t bytes) {

@@ -58,11 +58,29 @@ __global__ void __launch_bounds__(NT_W) k_dwt_level(const R* __restrict__ x0, co
         g[j] = ((j & 1) ? R(-1) : R(1)) * filt[k * MAX_FILTER + lf - 1 - j];
     }
     const R* src = level == 0 ? x0 : ll_in + (int64_t)k * (ny / 2) * (nx / 2);
-    for (int i = threadIdx.x; i < IH * IW; i += blockDim.x) {
+    const int64_t boff = (int64_t)k * ny * nx;
+    const bool last = level == L - 1;
+    // step 13 reads the current s of this thread's outputs: issue those loads first
+    constexpr int PER = AT * AT / NT_W;
+    R s_old[PER][4];
+    if (MODE == 1) {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int i = threadIdx.x + q * NT_W;
+            if (i < ty * tx) {
+                const int oy = oy0 + i / tx, ox = ox0 + i % tx;
+                s_old[q][0] = out[boff + (int64_t)oy * nx + hx + ox];
+                s_old[q][1] = out[boff + (int64_t)(hy + oy) * nx + ox];
+                s_old[q][2] = out[boff + (int64_t)(hy + oy) * nx + hx + ox];
+                s_old[q][3] = last ? out[boff + (int64_t)oy * nx + ox] : R(0);
+            }
+        }
+    }
+    stage_batched<8>(in, IH * IW, [&](int i) {
         const int r = i / IW, c = i - r * IW;
         const int gy = (2 * oy0 + r) & (my - 1), gx = (2 * ox0 + c) & (mx - 1);
-        in[i] = src[(int64_t)gy * mx + gx];
-    }
+        return src[(int64_t)gy * mx + gx];
+    });
     __syncthreads();
     for (int i = threadIdx.x; i < IH * tx; i += blockDim.x) {
         const int r = i / tx, c = i - r * tx;
@@ -73,9 +91,10 @@ __global__ void __launch_bounds__(NT_W) k_dwt_level(const R* __restrict__ x0, co
         rd[i] = d;
     }
     __syncthreads();
-    const int64_t boff = (int64_t)k * ny * nx;
-    const bool last = level == L - 1;
-    for (int i = threadIdx.x; i < ty * tx; i += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = threadIdx.x + q * NT_W;
+        if (i >= ty * tx) break;
         const int r = i / tx, c = i - r * tx;
         R ll = 0, hl = 0, lh = 0, hh = 0;
         for (int j = 0; j < lf; ++j) {
@@ -93,10 +112,10 @@ __global__ void __launch_bounds__(NT_W) k_dwt_level(const R* __restrict__ x0, co
             if (last) out[p_ll] = ll * scale;
         } else {
             R so, sn;
-            so = out[p_hl]; sn = clip(so + hl * scale, alpha); out[p_hl] = sn; ds[p_hl] = sn - so;
-            so = out[p_lh]; sn = clip(so + lh * scale, alpha); out[p_lh] = sn; ds[p_lh] = sn - so;
-            so = out[p_hh]; sn = clip(so + hh * scale, alpha); out[p_hh] = sn; ds[p_hh] = sn - so;
-            if (last) { so = out[p_ll]; sn = clip(so + ll * scale, alpha); out[p_ll] = sn; ds[p_ll] = sn - so; }
+            so = s_old[q][0]; sn = clip(so + hl * scale, alpha); out[p_hl] = sn; ds[p_hl] = sn - so;
+            so = s_old[q][1]; sn = clip(so + lh * scale, alpha); out[p_lh] = sn; ds[p_lh] = sn - so;
+            so = s_old[q][2]; sn = clip(so + hh * scale, alpha); out[p_hh] = sn; ds[p_hh] = sn - so;
+            if (last) { so = s_old[q][3]; sn = clip(so + ll * scale, alpha); out[p_ll] = sn; ds[p_ll] = sn - so; }
         }
         if (!last) ll_out[(int64_t)k * (ny / 2) * (nx / 2) + (int64_t)oy * hx + ox] = ll;
     }
@@ -143,13 +162,26 @@ __device__ void synth_tile(const R* __restrict__ coef, const R* __restrict__ ll_
     const int64_t boff = (int64_t)k * ny * nx;
     const bool coarsest = level == L - 1;
     const R* llsrc = ll_in + (int64_t)k * (ny / 2) * (nx / 2);
-    for (int i = threadIdx.x; i < NKy * NKx; i += blockDim.x) {
-        const int r = i / NKx, c = i - r * NKx;
-        const int gy = (kby + r) & (hy - 1), gx = (kbx + c) & (hx - 1);
-        LLs[i] = coarsest ? coef[boff + (int64_t)gy * nx + gx] : llsrc[(int64_t)gy * hx + gx];
-        HLs[i] = coef[boff + (int64_t)gy * nx + hx + gx];
-        LHs[i] = coef[boff + (int64_t)(hy + gy) * nx + gx];
-        HHs[i] = coef[boff + (int64_t)(hy + gy) * nx + hx + gx];
+    constexpr int UB = 2;                 // rows of the strided loop whose loads go out together
+    for (int base = threadIdx.x; base < NKy * NKx; base += UB * (int)blockDim.x) {
+        R v[UB][4];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int i = base + u * (int)blockDim.x;
+            if (i < NKy * NKx) {
+                const int r = i / NKx, c = i - r * NKx;
+                const int gy = (kby + r) & (hy - 1), gx = (kbx + c) & (hx - 1);
+                v[u][0] = coarsest ? coef[boff + (int64_t)gy * nx + gx] : llsrc[(int64_t)gy * hx + gx];
+                v[u][1] = coef[boff + (int64_t)gy * nx + hx + gx];
+                v[u][2] = coef[boff + (int64_t)(hy + gy) * nx + gx];
+                v[u][3] = coef[boff + (int64_t)(hy + gy) * nx + hx + gx];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int i = base + u * (int)blockDim.x;
+            if (i < NKy * NKx) { LLs[i] = v[u][0]; HLs[i] = v[u][1]; LHs[i] = v[u][2]; HHs[i] = v[u][3]; }
+        }
     }
     __syncthreads();
     const int off = lf / 2 - 1;
