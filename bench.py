@@ -131,6 +131,33 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+# committed ncu summaries with the measured DRAM traffic of a kernel, per bench phase
+PROFILE_OF_PHASE = {"grid_dual": "k_grid8c_gridding_c5.md", "degrid_dual": "k_degrid_degridding_c5.md"}
+
+
+def measured_traffic(phase, workload):
+    """DRAM read + write bytes per launch of a phase's kernel from its committed ncu
+    summary, or None when there is none or the kernel's source file no longer has the
+    hash recorded at capture time (the counters then describe another kernel)."""
+    import hashlib
+    import re
+    name = PROFILE_OF_PHASE.get(phase)
+    if name is None or workload != "c5":
+        return None
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_src = re.search(r"`([^`]+\.cu)` sha256 ([0-9a-f]{64})", text)
+    m_tr = re.search(r"traffic per launch \(DRAM read \+ write\) \| (\d+) B", text)
+    if not m_src or not m_tr:
+        return None
+    src = os.path.join(ROOT, m_src.group(1))
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != m_src.group(2):
+        return None
+    return int(m_tr.group(1))
+
+
 def job_throughput(ms_local, steps, device="cuda"):
     """Max over ranks of the timed region (ms) and the whole-job throughput. Every rank
     solves its own problem (weak scaling), so value = world * steps / max time."""
@@ -303,7 +330,7 @@ def run_ours(args):
     achieved = kernels[dom]["GBps"]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": None, "algorithmic_bytes_per_launch": int(alg[dom])}
+                "traffic": measured_traffic(dom, args.workload), "algorithmic_bytes_per_launch": int(alg[dom])}
 
     # ---- Phi / Phi^H alone, and cuFFT as a timed comparison of the FFT passes
     operators = None
