@@ -222,6 +222,11 @@ typedef struct {
     int32_t use_graph;             /* 1: capture one iteration in a CUDA graph and replay it */
     int32_t profile;               /* 1 (and use_graph = 0): time every kernel phase with CUDA
                                       events on `stream`; synchronises after each iteration */
+    int32_t adapt_exact;           /* with adaptive = 1: 0 takes c_i (Sec. 4) from ||G_i b - y_i|| of
+                                      the last iteration block i was active (free, lagged); 1 takes
+                                      it from ||Phi_i x^(t) - y_i|| of every block after every
+                                      iteration (Sec. 4's definition; one extra forward FFT and a
+                                      degridding pass over all visibilities per iteration) */
 } pd_params;
 
 /*

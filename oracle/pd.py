@@ -15,7 +15,9 @@ notation. Plain choices where the paper is silent:
   ||G_i b_i - y_i|| computed in step 8 of the last iteration in which block i
   was active (that is, Phi_i applied to x~ of the previous iteration); the
   initial norms come from one full pass with x^(0). p^(t) is computed before the
-  draw of iteration t.
+  draw of iteration t. With adaptive["exact"] the norms are instead
+  ||Phi_i x^(t) - y_i|| of the primal iterate after every iteration, for all
+  blocks (Sec. 4 defines c_i on Phi_i x^(t); this costs one full Phi per iteration).
 * The stopping rule "until convergence" (step 19) is a fixed iteration count.
 """
 import numpy as np
@@ -136,6 +138,9 @@ def pd_iteration(problem, st, tau, sigma, varsigma, kappa, psi_norm, seed,
     # step 18: over-relaxation
     st.x_tilde = 2.0 * x_new - st.x
     st.x = x_new
+    if adaptive is not None and adaptive.get("exact", False):
+        # Sec. 4, exact reading: c_i for the next draw from Phi_i x^(t) of every block
+        st.res_norm = block_residuals(problem, st.x)
     return active, active_basis
 
 

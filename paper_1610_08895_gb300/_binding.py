@@ -39,7 +39,8 @@ class PdParams(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("psi_norm", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("p_block", ctypes.c_void_p), ("p_basis", ctypes.c_void_p), ("adaptive", ctypes.c_int32),
                 ("adapt_n", ctypes.c_double), ("adapt_p_min", ctypes.c_double),
-                ("adapt_p_max", ctypes.c_double), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("adapt_p_max", ctypes.c_double), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("adapt_exact", ctypes.c_int32)]
 
 
 _lib = None

@@ -176,6 +176,7 @@ class State:
             prm.adapt_n = float(adaptive["n"])
             prm.adapt_p_min = float(adaptive["p_min"])
             prm.adapt_p_max = float(adaptive["p_max"])
+            prm.adapt_exact = int(bool(adaptive.get("exact", False)))
         B.call("pd_iterate", p.handle, self._h, ctypes.byref(prm), int(niter), _stream())
 
     def x(self):

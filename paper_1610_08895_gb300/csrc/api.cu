@@ -624,7 +624,14 @@ static cudaError_t enqueue_iteration(pd_plan* p, pd_state* st, const pd_params* 
     if (concurrent && (e = cudaStreamWaitEvent(s, st->ev_join, 0))) return e;
     PrimalArgs pa{prm->tau, prm->sigma, prm->varsigma, st->x, st->xt, st->st, st->prim_part};
     if ((e = inv_fft<R>(p, (const cplx_t<R>*)st->u, nullptr, &pa, s))) return e;
-    return primal_finish(p, st, s);
+    if ((e = primal_finish(p, st, s))) return e;
+    if (prm->adaptive && prm->adapt_exact) {
+        // Sec. 4: c_i of the next draw from ||Phi_i x^(t) - y_i|| of every block
+        if ((e = fwd_fft<R>(p, (const R*)st->x, (cplx_t<R>*)p->gridb, s))) return e;
+        if ((e = degrid_res_norms<R>(p, (const cplx_t<R>*)p->gridb, (const cplx_t<R>*)st->y, st->res_norm, s)))
+            return e;
+    }
+    return cudaSuccess;
 }
 
 static std::vector<unsigned char> params_key(const pd_plan* p, const pd_params* prm, cudaStream_t s) {
@@ -637,6 +644,7 @@ static std::vector<unsigned char> params_key(const pd_plan* p, const pd_params* 
     put(&prm->kappa, sizeof(double)); put(&prm->psi_norm, sizeof(double)); put(&prm->seed, sizeof(uint64_t));
     put(&prm->adaptive, sizeof(int32_t)); put(&prm->adapt_n, sizeof(double));
     put(&prm->adapt_p_min, sizeof(double)); put(&prm->adapt_p_max, sizeof(double));
+    put(&prm->adapt_exact, sizeof(int32_t));
     put(&s, sizeof(s));
     (void)p;
     return k;

@@ -230,14 +230,15 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
 // block: lane-strided partial sums, then a fixed shuffle tree), the ball scale
 // c_i = max(0, 1 - eps_i/||r_i||) of step 8 (so v_new = c_i r_i = z - P_B(z)), and the
 // residual norm ||G_i b - y_i|| for the adaptive probabilities of Sec. 4.
+// norm_only (active == nullptr: every block): only the residual norm is written.
 template <typename R>
 __global__ void k_block_norms(const double* __restrict__ part, const int32_t* __restrict__ bss,
                               const int32_t* __restrict__ bsl, const int32_t* __restrict__ active,
                               const double* __restrict__ eps, double* __restrict__ bnorm, R* __restrict__ scale,
-                              double* __restrict__ res_norm, int d) {
+                              double* __restrict__ res_norm, int d, int norm_only) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (i >= d || !active[i]) return;     // whole warps leave together
+    if (i >= d || (active && !active[i])) return;     // whole warps leave together
     double sr = 0.0, sd = 0.0;
     for (int k = bss[i] + lane; k < bss[i + 1]; k += 32) {
         const int sg = bsl[k];
@@ -247,6 +248,10 @@ __global__ void k_block_norms(const double* __restrict__ part, const int32_t* __
     sr = warp_sum(sr);
     sd = warp_sum(sd);
     if (lane != 0) return;
+    if (norm_only) {
+        res_norm[i] = sqrt(sd);
+        return;
+    }
     bnorm[2 * i] = sr;
     bnorm[2 * i + 1] = sd;
     const double nr = sqrt(sr);
@@ -600,8 +605,24 @@ cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs&
     prof_mark(PH_NORMS, 0, s);
     k_block_norms<R><<<(p->d * 32 + 127) / 128, 128, 0, s>>>(p->seg_part, p->block_seg_start, p->block_seg_list,
                                                        a.block_active, a.eps, p->blk_norm, (R*)p->blk_scale,
-                                                       a.res_norm, p->d);
+                                                       a.res_norm, p->d, 0);
     prof_mark(PH_NORMS, 1, s);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t degrid_res_norms(const pd_plan* p, const cplx_t<R>* grid, const cplx_t<R>* y, double* res_norm,
+                             cudaStream_t s) {
+    // every block: the residual part of the pd-mode pass (its r output goes to the
+    // plan's scratch and v is not needed, so y stands in for it), then ||G_i b - y_i||
+    const int ctas = std::min(p->g.ntiles, p->num_sms * 8);
+    DualArgs a{y, (void*)y, nullptr, nullptr, res_norm};
+    cudaError_t e = cudaSuccess;
+    PD_J_DISPATCH(p->g.J, (e = launch_degrid<R, JJ, 1>(p, grid, nullptr, &a, p->tile_order, p->counts_all + 1,
+                                                        ctas, s)));
+    if (e) return e;
+    k_block_norms<R><<<(p->d * 32 + 127) / 128, 128, 0, s>>>(p->seg_part, p->block_seg_start, p->block_seg_list,
+                                                       nullptr, nullptr, nullptr, nullptr, res_norm, p->d, 1);
     return cudaGetLastError();
 }
 
@@ -672,6 +693,8 @@ cudaError_t grid_dual(const pd_plan* p, const DualArgs& a, const int32_t* tiles,
 
 template cudaError_t degrid_plain<float>(const pd_plan*, const float2*, float2*, cudaStream_t);
 template cudaError_t degrid_plain<double>(const pd_plan*, const double2*, double2*, cudaStream_t);
+template cudaError_t degrid_res_norms<float>(const pd_plan*, const float2*, const float2*, double*, cudaStream_t);
+template cudaError_t degrid_res_norms<double>(const pd_plan*, const double2*, const double2*, double*, cudaStream_t);
 template cudaError_t degrid_dual<float>(const pd_plan*, const float2*, const DualArgs&, const int32_t*,
                                         const int32_t*, cudaStream_t);
 template cudaError_t degrid_dual<double>(const pd_plan*, const double2*, const DualArgs&, const int32_t*,

@@ -189,6 +189,10 @@ struct DualArgs {
 // plain degrid: out (user order) = G grid
 template <typename R>
 cudaError_t degrid_plain(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out_user, cudaStream_t s);
+// ||G_i grid - y_i|| of every block into res_norm (the exact reading of Sec. 4's c_i)
+template <typename R>
+cudaError_t degrid_res_norms(const pd_plan* p, const cplx_t<R>* grid, const cplx_t<R>* y, double* res_norm,
+                             cudaStream_t s);
 // pd degrid over the listed tiles: r = v + G b - y, segment partial norms, then block scales
 template <typename R>
 cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs& a, const int32_t* tiles,

@@ -123,3 +123,20 @@ def test_tile_autotuner_picks_a_working_tile():
                                 basis_ids=prob.basis_ids, levels=prob.levels, candidates=(4, 16, 32, 64), iters=3)
     assert times[4] < 0                      # below the kernel width: rejected by the plan
     assert best in (16, 32, 64) and times[best] == min(t for t in times.values() if t > 0)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_adaptive_probabilities_exact_reading(use_graph):
+    # Sec. 4's c_i from ||Phi_i x^(t) - y_i|| of every block after every iteration
+    prob, _ = make_problem(64, 16384, 16, 8, (0, 1, 2), 2, uv_kind="radial", blocks="annuli", nannuli=16)
+    kw = _steps(prob)
+    ad = {"n": 4.0, "p_min": 0.05, "p_max": 0.5, "exact": True}
+    niter = 30
+    st_ref, draws = PD.pd_run(prob, niter, seed=3, p_block=None, p_basis=[1.0] * 3, adaptive=ad, **kw)
+    plan, st = _setup(prob, "f32")
+    st.pd_iterate(niter, seed=3, p_basis=[1.0] * 3, adaptive=ad, use_graph=use_graph, **kw)
+    rep = st.report()
+    assert list(rep["block_active"]) == list(draws[-1][0])
+    assert rel(st.x().cpu().numpy(), st_ref.x) < TOL_IT32
+    assert np.allclose(rep["res_norm"], st_ref.res_norm, rtol=1e-4)
+    assert rep["p_block"].sum() == pytest.approx(4.0, rel=1e-9)

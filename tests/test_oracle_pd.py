@@ -156,3 +156,28 @@ def test_adaptive_pd_runs_and_keeps_probability_budget():
         act, _ = PD.pd_iteration(prob, st, 0.49, 1.0, 1e-3, 0.1, 1.0, 2, None, [1.0] * 2, adaptive=ad)
         counts += sum(act)
     assert 0 < counts < 40 * 4
+
+
+def test_exact_adaptive_with_full_budget_is_the_deterministic_run():
+    # n = d forces every p_i = 1 (sum p_i = n, p_i <= 1), whatever the c_i: the exact
+    # reading must then reproduce the deterministic Algorithm 1 exactly
+    prob, _ = tiny_problem(nblocks=4, m=256)
+    kw = dict(tau=0.49, sigma=1.0, varsigma=1e-3, kappa=0.1, psi_norm=1.0, seed=2, p_basis=[1.0] * 2)
+    st_det, _ = PD.pd_run(prob, 25, p_block=[1.0] * 4, **kw)
+    st_ex, draws = PD.pd_run(prob, 25, p_block=None, adaptive={"n": 4.0, "p_min": 0.05, "p_max": 1.0,
+                                                             "exact": True}, **kw)
+    assert all(all(a) for a, _ in draws)
+    assert np.array_equal(st_ex.x, st_det.x)
+
+
+def test_exact_adaptive_norms_are_those_of_the_current_iterate():
+    # the exact reading keeps ||Phi_i x^(t) - y_i|| for every block (Sec. 4), whereas the
+    # lagged reading keeps the norm of the last pass in which the block was active
+    prob, _ = tiny_problem(nblocks=4, m=256)
+    st = PD.PDState(prob)
+    ad = {"n": 1.0, "p_min": 0.05, "p_max": 0.5, "exact": True}
+    for _ in range(10):
+        PD.pd_iteration(prob, st, 0.49, 1.0, 1e-3, 0.1, 1.0, 2, None, [1.0] * 2, adaptive=ad)
+        direct = np.array([np.linalg.norm(meas.Geometry(8, 8, 4).phi(st.x, prob.uv[ix]) - prob.y[ix])
+                           for ix in prob.block_index])
+        assert np.allclose(st.res_norm, direct, rtol=1e-12)
