@@ -135,11 +135,30 @@ class Clocks:
 PROFILE_OF_PHASE = {"grid_dual": "k_grid8c_gridding_c5.md", "degrid_dual": "k_degrid_degridding_c5.md"}
 
 
+def kernel_source_hash(path, name):
+    """sha256 of a kernel's definition text in a .cu file (from `__global__` to the
+    closing brace of its body), or None if the kernel is not found."""
+    import hashlib
+    import re
+    text = open(path).read()
+    m = re.search(r"__global__ void(?:\s+__launch_bounds__\([^)]*\))?\s+" + re.escape(name) + r"\(", text)
+    if not m:
+        return None
+    depth = 0
+    for j in range(text.index("{", m.end()), len(text)):
+        if text[j] == "{":
+            depth += 1
+        elif text[j] == "}":
+            depth -= 1
+            if depth == 0:
+                return hashlib.sha256(text[m.start():j + 1].encode()).hexdigest()
+    return None
+
+
 def measured_traffic(phase, workload):
     """DRAM read + write bytes per launch of a phase's kernel from its committed ncu
-    summary, or None when there is none or the kernel's source file no longer has the
+    summary, or None when there is none or the kernel's definition no longer has the
     hash recorded at capture time (the counters then describe another kernel)."""
-    import hashlib
     import re
     name = PROFILE_OF_PHASE.get(phase)
     if name is None or workload != "c5":
@@ -148,12 +167,12 @@ def measured_traffic(phase, workload):
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m_src = re.search(r"`([^`]+\.cu)` sha256 ([0-9a-f]{64})", text)
+    m_src = re.search(r"`([^`]+\.cu)` kernel `(\w+)` sha256 ([0-9a-f]{64})", text)
     m_tr = re.search(r"traffic per launch \(DRAM read \+ write\) \| (\d+) B", text)
     if not m_src or not m_tr:
         return None
     src = os.path.join(ROOT, m_src.group(1))
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != m_src.group(2):
+    if not os.path.exists(src) or kernel_source_hash(src, m_src.group(2)) != m_src.group(3):
         return None
     return int(m_tr.group(1))
 

@@ -26,7 +26,10 @@ def test_traffic_dropped_once_the_kernel_source_changes(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     orig = bench.measured_traffic("grid_dual", "c5")
     with open(tmp_path / src_rel, "a") as f:
-        f.write("\n// edited\n")
+        f.write("\n// an edit elsewhere in the file keeps the kernel's counters\n")
+    assert bench.measured_traffic("grid_dual", "c5") == orig
+    text = (tmp_path / src_rel).read_text()
+    (tmp_path / src_rel).write_text(text.replace("const int pk = scl[warp][q];", "const int pk = scl[warp][q] + 0;"))
     assert bench.measured_traffic("grid_dual", "c5") is None
     if orig is not None:       # the copy matched its recorded hash before the edit
         assert orig > 0
