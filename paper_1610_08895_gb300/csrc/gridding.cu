@@ -576,6 +576,12 @@ static cudaError_t launch_degrid(const pd_plan* p, const cplx_t<R>* grid, cplx_t
     const size_t smem = win * sizeof(cplx_t<R>) + (size_t)16 * ms * sizeof(double) + (size_t)(2 * ms + 1) * sizeof(int);
     cudaError_t e = ensure_smem(k_degrid<R, J, MODE>, smem);
     if (e) return e;
+    // CTAs stride over the heaviest-first tile list: launch only as many as are
+    // resident at once, so none starts its share late
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid<R, J, MODE>, 256, smem) == cudaSuccess &&
+        per_sm > 0)
+        ctas = std::min(ctas, per_sm * p->num_sms);
     k_degrid<R, J, MODE><<<ctas, 256, smem, s>>>(
         grid, out, a ? (const cplx_t<R>*)a->y : nullptr, a ? (const cplx_t<R>*)a->v : nullptr,
         (cplx_t<R>*)p->rbuf, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start, p->seg_block,
