@@ -385,7 +385,7 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
         st2.close()
 
-    # ---- the same workload with FP64 bulk data (the benchmark spec's FP64 comparison form)
+    # ---- the same workload with FP64 bulk data (the plain FP64 form, for comparison)
     fp64 = None
     if not args.no_fp64:
         plan64 = Plan(n, n, uv, blk, d, kernel_width=cfg["J"], basis_ids=cfg["bases"], levels=cfg["levels"],
