@@ -50,3 +50,41 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_binding, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(_binding.ExtensionMissing):
         _binding.load()
+
+
+def test_plan_descriptions_are_refused_before_any_device_work(lib):
+    """Invalid or unsupported plan descriptions return a status and a message without
+    touching a GPU (this runs on machines that have none)."""
+    from paper_1610_08895_gb300 import _binding as B
+    m = 16
+    uv = np.zeros((m, 2))
+    blk = np.zeros(m, np.int32)
+    ids = np.array([0, 1], np.int32)
+    bad_ids = np.array([0, 9], np.int32)
+
+    def create(**over):
+        kw = dict(nx=64, ny=64, osf=2, nvis=m, uv=uv.ctypes.data, nblocks=1, block_of_vis=blk.ctypes.data,
+                  kernel_width=8, kb_beta=0.0, nbases=2, basis_ids=ids.ctypes.data, levels=2,
+                  precision=B.PD_F32, tile=0)
+        kw.update(over)
+        d = B.PdPlanDesc(**kw)
+        h = ctypes.c_void_p()
+        st = lib.pd_plan_create(ctypes.byref(d), ctypes.byref(h))
+        return st, lib.pd_last_error()
+
+    cases = [
+        (dict(nx=48), 1, b"powers of two"),
+        (dict(ny=8), 1, b"powers of two"),
+        (dict(osf=3), 1, b"oversampling"),
+        (dict(nx=8192, ny=8192, precision=B.PD_F64), 6, b"FP64"),
+        (dict(kernel_width=7), 1, b"kernel_width"),
+        (dict(nblocks=0), 1, b"nblocks"),
+        (dict(basis_ids=bad_ids.ctypes.data), 1, b"basis ids"),
+        (dict(levels=7, nx=16, ny=16), 1, b"levels"),
+        (dict(tile=4), 1, b"tile"),
+        (dict(precision=7), 1, b"precision"),
+    ]
+    for over, status, text in cases:
+        st, msg = create(**over)
+        assert st == status, (over, st, msg)
+        assert text in msg, (over, msg)
