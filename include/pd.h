@@ -70,7 +70,7 @@ typedef struct pd_state pd_state;
  *               (Sec. 5 uses 8 x 8).
  * kb_beta       Kaiser-Bessel shape; 0 selects pi*sqrt((J/2)^2*1.5^2 - 0.8).
  * nbases        b in [1, 16]; basis_ids host [b]: 0 = Dirac, k = db_k (1..8).
- * levels        wavelet levels L >= 1 with nx >> L >= 1 and ny >> L >= 1.
+ * levels        wavelet levels 1 <= L <= 13 with nx >> L >= 1 and ny >> L >= 1.
  * precision     PD_F32 (complex64 bulk data, FP64 reductions) or PD_F64.
  * tile          gridding tile edge in cells (power of two, >= J); 0 = choose.
  */
@@ -154,23 +154,27 @@ pd_status pd_apply_psi_adj(pd_plan* plan, const void* x, void* coeffs, void* str
 /*
  * Psi^H x without a plan and without allocating device memory (the paper has no
  * counterpart; this is a deployment variant of pd_apply_psi_adj). For callers
- * that cannot call cudaMalloc once they are running: code that must keep a fixed
- * device-memory budget, or that runs where allocation is not allowed, such as
- * between the start and end of a CUDA-graph stream capture. The output equals
+ * that cannot call cudaMalloc once they are running: code that must keep to a
+ * device-memory budget fixed at start-up (a real-time pipeline that reserves all
+ * of its memory up front, or a host application whose own pool owns the device
+ * memory), where a plan's allocations would break that budget. The output equals
  * pd_apply_psi_adj's for the same image, bases and levels.
  *
  * x: device real [ny][nx]; coeffs: device real [nbases][ny][nx] (packed layout,
- * scaled by nbases^{-1/2}); basis_ids: host [nbases] (0 = Dirac, k = db_k);
- * precision PD_F32 / PD_F64 selects float / double data.
+ * scaled by nbases^{-1/2}); basis_ids: host [nbases] (0 = Dirac, k = db_k), read
+ * during the call only (it travels to the GPU as a kernel argument);
+ * precision PD_F32 / PD_F64 selects float / double data; 1 <= levels <= 13.
  * Scratch: the library's file-scope 16 MiB device array (held by every GPU that
  * loads the library until exit). Calls needing more than it holds -- about
- * 2 * nbases * (ny/2) * (nx/2) elements plus the filter table -- fail with
+ * 2 * nbases * (ny/2) * (nx/2) elements plus the filter tables -- fail with
  * PD_EINVAL and a message naming the size. Every call shares the array, so calls
  * that overlap on the GPU (different streams, or different host threads without
- * ordering) race; order them on one stream.
- * The first call on a device does a one-time set-up (looks up the array's device
- * address with that device current, derives the Daubechies filters on the host);
- * make that first call before any stream capture. Asynchronous on `stream`.
+ * ordering) race; order them on one stream. `stream` must belong to the current
+ * device (PD_EINVAL otherwise); NULL is the current device's legacy stream.
+ * The first call on a device does a one-time set-up: it looks up the array's
+ * device address with that device current and writes the Daubechies filter tables
+ * into the array with a synchronous copy; make that first call before any stream
+ * capture. Later calls copy nothing from host memory. Asynchronous on `stream`.
  */
 pd_status pd_apply_psi_adj_noalloc(const void* x, void* coeffs, int32_t nx, int32_t ny, int32_t levels,
                                    const int32_t* basis_ids, int32_t nbases, int32_t precision,

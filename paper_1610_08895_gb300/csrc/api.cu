@@ -131,8 +131,9 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
     if (d->nbases < 1 || d->nbases > MAX_BASES || !d->basis_ids) return fail(PD_EINVAL, "nbases must be in [1, 16]");
     for (int k = 0; k < d->nbases; ++k)
         if (d->basis_ids[k] < 0 || d->basis_ids[k] > 8) return fail(PD_EINVAL, "basis ids must be 0 (Dirac) or 1..8");
-    if (d->levels < 1 || (d->nx >> d->levels) < 1 || (d->ny >> d->levels) < 1)
-        return fail(PD_EINVAL, "levels must satisfy 1 <= L and n >> L >= 1");
+    // bounded before the shift test (a shift by 32 or more is undefined)
+    if (d->levels < 1 || d->levels > 13 || (d->nx >> d->levels) < 1 || (d->ny >> d->levels) < 1)
+        return fail(PD_EINVAL, "levels must satisfy 1 <= L <= 13 and n >> L >= 1");
     if (d->precision != PD_F32 && d->precision != PD_F64) return fail(PD_EINVAL, "precision must be PD_F32 or PD_F64");
     if (d->kb_beta < 0) return fail(PD_EINVAL, "kb_beta must be >= 0");
     if (d->tile != 0 && (!is_pow2(d->tile) || d->tile < d->kernel_width))

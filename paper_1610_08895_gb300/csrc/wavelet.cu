@@ -401,34 +401,30 @@ cudaError_t sparsity_dual(const pd_plan* p, const R* xt, R* s, R* st, const int3
 
 // -------------------------------------------------------------------- allocation-free analysis
 // pd_apply_psi_adj_noalloc runs the same analysis kernels as pd_apply_psi_adj, but
-// without a plan: its scratch (the two approximation buffers of the level loop, the
-// filter table, the basis flags) lives in this file-scope device array instead of
-// memory allocated with cudaMalloc. Every GPU that loads the library holds the array
-// until exit; every call shares it.
+// without a plan: its scratch lives in this file-scope device array instead of memory
+// allocated with cudaMalloc. Every GPU that loads the library holds the array until
+// exit; every call shares it. Layout: the db1..db8 filter tables in FP64 and FP32
+// (written once per device at set-up), then the per-call region: the filter table and
+// flags of the call's bases (written by a kernel from its by-value arguments, so a call
+// never copies from host memory) and the two approximation buffers of the level loop.
 constexpr size_t PSI_STATIC_BYTES = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_psi_static[PSI_STATIC_BYTES];
+
+static size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+constexpr size_t DB_TAB_D = 9 * MAX_FILTER * sizeof(double);   // [9][16], row 0 (Dirac) all zero
+constexpr size_t DB_TAB_F = 9 * MAX_FILTER * sizeof(float);
+static size_t psi_static_fixed() { return align256(DB_TAB_D) + align256(DB_TAB_F); }
 
 static std::mutex g_psi_static_mu;
 static void* g_psi_static_addr[64];       // device address of g_psi_static, per device
 static int g_psi_static_sms[64];
-static bool g_db_ready = false;
-static double g_db_d[9][MAX_FILTER];      // db_k low-pass filters (k = 1..8), FP64
-static float g_db_f[9][MAX_FILTER];
 
-static size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
-
-// One-time set-up for the current device: the device address of the static array (host
-// code may not use the symbol itself as a pointer) and the Daubechies table.
+// One-time set-up for device `dev` (current): the device address of the static array
+// (host code may not use the symbol itself as a pointer), the SM count, and the
+// Daubechies tables, written with a synchronous copy before the first call's kernels.
 static pd_status psi_static_setup(int dev, void** addr, int* sms) {
     std::lock_guard<std::mutex> lock(g_psi_static_mu);
     if (dev < 0 || dev >= 64) return set_error(PD_ENOTSUP, "pd_apply_psi_adj_noalloc: device index above 63");
-    if (!g_db_ready) {
-        for (int k = 1; k <= 8; ++k) {
-            const std::vector<double> h = daubechies(k);
-            for (size_t j = 0; j < h.size(); ++j) { g_db_d[k][j] = h[j]; g_db_f[k][j] = (float)h[j]; }
-        }
-        g_db_ready = true;
-    }
     if (!g_psi_static_addr[dev]) {
         void* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_psi_static);
@@ -437,6 +433,15 @@ static pd_status psi_static_setup(int dev, void** addr, int* sms) {
         int n = 0;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return set_error(PD_ECUDA, "pd_apply_psi_adj_noalloc: cannot query the SM count");
+        std::vector<unsigned char> tab(psi_static_fixed(), 0);
+        double* td = (double*)tab.data();
+        float* tf = (float*)(tab.data() + align256(DB_TAB_D));
+        for (int k = 1; k <= 8; ++k) {
+            const std::vector<double> h = daubechies(k);
+            for (size_t j = 0; j < h.size(); ++j) { td[k * MAX_FILTER + j] = h[j]; tf[k * MAX_FILTER + j] = (float)h[j]; }
+        }
+        if (cudaMemcpy(ptr, tab.data(), tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return set_error(PD_ECUDA, "pd_apply_psi_adj_noalloc: writing the filter tables failed");
         g_psi_static_addr[dev] = ptr;
         g_psi_static_sms[dev] = n;
     }
@@ -445,35 +450,50 @@ static pd_status psi_static_setup(int dev, void** addr, int* sms) {
     return PD_OK;
 }
 
+// The call's bases, passed by value as a kernel argument.
+struct BasisList {
+    int32_t id[MAX_BASES];
+    int32_t b;
+};
+
+// Per-call filter table [b][MAX_FILTER], filter lengths and all-active flags of the
+// call's bases, from the static db tables.
+template <typename R>
+__global__ void k_psi_call_tables(BasisList bl, const R* __restrict__ db, R* __restrict__ filt,
+                                  int32_t* __restrict__ flen, int32_t* __restrict__ ones) {
+    const int i = threadIdx.x;
+    if (i >= bl.b * MAX_FILTER) return;
+    const int k = i / MAX_FILTER, j = i - k * MAX_FILTER;
+    const int id = bl.id[k];
+    filt[i] = db[id * MAX_FILTER + j];
+    if (j == 0) {
+        flen[k] = id == 0 ? 0 : 2 * id;
+        ones[k] = 1;
+    }
+}
+
 template <typename R>
 static pd_status psi_adj_static_t(const R* x, R* coeffs, int nx, int ny, int L, const int32_t* ids, int b,
                                   unsigned char* scratch, int sms, cudaStream_t s) {
+    const R* db = (const R*)(scratch + (sizeof(R) == 8 ? 0 : align256(DB_TAB_D)));
+    unsigned char* call = scratch + psi_static_fixed();
     const size_t filt_bytes = align256((size_t)b * MAX_FILTER * sizeof(R));
     const size_t flag_bytes = align256((size_t)b * sizeof(int32_t));
     const size_t ll_bytes = align256((size_t)b * (ny / 2) * (nx / 2) * sizeof(R));
-    R* filt = (R*)scratch;
-    int32_t* flen = (int32_t*)(scratch + filt_bytes);
-    int32_t* ones = (int32_t*)(scratch + filt_bytes + flag_bytes);
-    R* ll[2] = {(R*)(scratch + filt_bytes + 2 * flag_bytes), (R*)(scratch + filt_bytes + 2 * flag_bytes + ll_bytes)};
-    // filter table and flags for this call, copied from host arrays of fixed size
-    R hf[MAX_BASES * MAX_FILTER];
-    int32_t hl[MAX_BASES], h1[MAX_BASES];
+    R* filt = (R*)call;
+    int32_t* flen = (int32_t*)(call + filt_bytes);
+    int32_t* ones = (int32_t*)(call + filt_bytes + flag_bytes);
+    R* ll[2] = {(R*)(call + filt_bytes + 2 * flag_bytes), (R*)(call + filt_bytes + 2 * flag_bytes + ll_bytes)};
+    BasisList bl{};
+    bl.b = b;
     int nwav = 0;
     for (int k = 0; k < b; ++k) {
-        const int id = ids[k];
-        hl[k] = id == 0 ? 0 : 2 * id;
-        h1[k] = 1;
-        nwav += id > 0;
-        for (int j = 0; j < MAX_FILTER; ++j)
-            hf[k * MAX_FILTER + j] = id == 0 || j >= 2 * id ? R(0) : (sizeof(R) == 8 ? (R)g_db_d[id][j] : (R)g_db_f[id][j]);
+        bl.id[k] = ids[k];
+        nwav += ids[k] > 0;
     }
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(filt, hf, (size_t)b * MAX_FILTER * sizeof(R), cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(flen, hl, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(ones, h1, (size_t)b * sizeof(int32_t), cudaMemcpyHostToDevice, s)))
-        return set_error(PD_ECUDA, cudaGetErrorString(e));
-    // copies from pageable host memory are staged before cudaMemcpyAsync returns, so the
-    // local arrays may go out of scope without a stream synchronisation
+    k_psi_call_tables<R><<<1, MAX_BASES * MAX_FILTER, 0, s>>>(bl, db, filt, flen, ones);
+    if ((e = cudaGetLastError())) return set_error(PD_ECUDA, cudaGetErrorString(e));
     const R scale = R(1.0 / std::sqrt((double)b));
     const int64_t n = (int64_t)ny * nx;
     const int dgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 4);
@@ -503,8 +523,9 @@ extern "C" pd_status pd_apply_psi_adj_noalloc(const void* x, void* coeffs, int32
     if (!x || !coeffs || !basis_ids) return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: null pointer");
     if (!pow2(nx) || !pow2(ny) || nx < 16 || ny < 16 || nx > 8192 || ny > 8192)
         return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: image sides must be powers of two in [16, 8192]");
-    if (levels < 1 || (nx >> levels) < 1 || (ny >> levels) < 1)
-        return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: levels must satisfy 1 <= L and n >> L >= 1");
+    // bounded before the shift test (a shift by 32 or more is undefined)
+    if (levels < 1 || levels > 13 || (nx >> levels) < 1 || (ny >> levels) < 1)
+        return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: levels must satisfy 1 <= L <= 13 and n >> L >= 1");
     if (nbases < 1 || nbases > MAX_BASES) return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: nbases in [1, 16]");
     for (int k = 0; k < nbases; ++k)
         if (basis_ids[k] < 0 || basis_ids[k] > 8)
@@ -512,8 +533,8 @@ extern "C" pd_status pd_apply_psi_adj_noalloc(const void* x, void* coeffs, int32
     if (precision != PD_F32 && precision != PD_F64)
         return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: precision must be PD_F32 or PD_F64");
     const size_t rsz = precision == PD_F64 ? 8 : 4;
-    const size_t need = align256((size_t)nbases * MAX_FILTER * rsz) + 2 * align256((size_t)nbases * 4) +
-                        2 * align256((size_t)nbases * (ny / 2) * (nx / 2) * rsz);
+    const size_t need = psi_static_fixed() + align256((size_t)nbases * MAX_FILTER * rsz) +
+                        2 * align256((size_t)nbases * 4) + 2 * align256((size_t)nbases * (ny / 2) * (nx / 2) * rsz);
     if (need > PSI_STATIC_BYTES) {
         static thread_local char msg[160];
         snprintf(msg, sizeof msg,
@@ -523,11 +544,19 @@ extern "C" pd_status pd_apply_psi_adj_noalloc(const void* x, void* coeffs, int32
     }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return set_error(PD_ECUDA, "pd_apply_psi_adj_noalloc: no current device");
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array's address is per device: the stream must belong to the current device
+    if (s != nullptr) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(s, &sdev) != cudaSuccess)
+            return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: cannot query the stream's device");
+        if (sdev != dev)
+            return set_error(PD_EINVAL, "pd_apply_psi_adj_noalloc: the stream belongs to another device than the current one");
+    }
     void* addr = nullptr;
     int sms = 0;
     pd_status st = psi_static_setup(dev, &addr, &sms);
     if (st != PD_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
     return precision == PD_F64
                ? psi_adj_static_t<double>((const double*)x, (double*)coeffs, nx, ny, levels, basis_ids, nbases,
                                           (unsigned char*)addr, sms, s)

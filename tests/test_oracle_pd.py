@@ -181,3 +181,38 @@ def test_exact_adaptive_norms_are_those_of_the_current_iterate():
         direct = np.array([np.linalg.norm(meas.Geometry(8, 8, 4).phi(st.x, prob.uv[ix]) - prob.y[ix])
                            for ix in prob.block_index])
         assert np.allclose(st.res_norm, direct, rtol=1e-12)
+
+
+def test_lagged_adaptive_norms_follow_the_last_active_pass():
+    # default reading of Sec. 4's c_i: after iteration t, an active block i holds
+    # ||Phi_i x~^(t-1) - y_i|| (the residual of step 8, on the x~ the iteration started
+    # from); an inactive block keeps its previous value bit for bit; before the first
+    # iteration every block holds ||Phi_i x^(0) - y_i|| = ||y_i||
+    prob, _ = tiny_problem(nblocks=4, m=256)
+    st = PD.PDState(prob)
+    assert np.array_equal(st.res_norm, np.array([np.linalg.norm(prob.y[ix]) for ix in prob.block_index]))
+    ad = {"n": 2.0, "p_min": 0.05, "p_max": 0.9}
+    geo = meas.Geometry(8, 8, 4)
+    seen_inactive = seen_active = 0
+    for _ in range(12):
+        xt_prev = st.x_tilde.copy()
+        prev = st.res_norm.copy()
+        act, _ = PD.pd_iteration(prob, st, 0.49, 1.0, 1e-3, 0.1, 1.0, 4, None, [1.0] * 2, adaptive=ad)
+        for i, ix in enumerate(prob.block_index):
+            if act[i]:
+                direct = np.linalg.norm(geo.phi(xt_prev, prob.uv[ix]) - prob.y[ix])
+                assert st.res_norm[i] == pytest.approx(direct, rel=1e-12)
+                seen_active += 1
+            else:
+                assert st.res_norm[i] == prev[i]
+                seen_inactive += 1
+    assert seen_active > 0 and seen_inactive > 0
+
+
+def test_snr_of_a_known_error():
+    # 20 log10(||x|| / ||x - x_hat||): x_hat = 0.9 x leaves 10% of ||x|| as error -> 20 dB
+    x = synth.test_image(16, seed=4)
+    assert EX.snr_db(x, 0.9 * x) == pytest.approx(20.0, abs=1e-12)
+    e = np.zeros_like(x)
+    e[3, 5] = 0.01 * np.linalg.norm(x)                           # one pixel off by 1% of ||x|| -> 40 dB
+    assert EX.snr_db(x, x + e) == pytest.approx(40.0, abs=1e-9)
