@@ -213,6 +213,18 @@ pd_status pd_state_destroy(pd_state* st);
 pd_status pd_state_set_data(pd_plan* plan, pd_state* st, const void* y, const double* eps,
                             void* stream);
 
+/*
+ * Start values of Algorithm 1 (step 1: x^(0), x~^(0), s^(0), v^(0) are given), for a
+ * warm start or a resumed reconstruction. Call after pd_state_set_data (it keeps y
+ * and eps). x0, x_tilde0: device real [ny][nx]; s0: device real [b][ny][nx]
+ * (packed layout); v0: device complex [nvis], user order; any of them may be NULL
+ * for zeros. Derives the state's s~ = Psi s^(0), U = G^T v^(0) and the adaptive
+ * residual norms ||Phi_i x^(0) - y_i||, and resets t to 0. Reads the inputs on
+ * `stream` and synchronises it before returning. Errors: PD_EINVAL, PD_ECUDA.
+ */
+pd_status pd_state_set_start(pd_plan* plan, pd_state* st, const void* x0, const void* x_tilde0,
+                             const void* s0, const void* v0, void* stream);
+
 /* Iteration parameters (host memory, read during pd_iterate). */
 typedef struct {
     double tau, sigma, varsigma;   /* step sizes (Sec. 3 convergence condition) */
@@ -231,6 +243,13 @@ typedef struct {
                                       it from ||Phi_i x^(t) - y_i|| of every block after every
                                       iteration (Sec. 4's definition; one extra forward FFT and a
                                       degridding pass over all visibilities per iteration) */
+    int32_t per_block;             /* 1: the plain per-block form, for comparison with the batched
+                                      one: the host draws the active sets (same Philox draws) and
+                                      launches the degridding, ball projection, gridding and halo
+                                      merge once per active block and the wavelet analysis and
+                                      synthesis once per active basis; same results up to rounding
+                                      order. Needs adaptive = 0 and use_graph = 0; synchronises
+                                      `stream` after every iteration. */
 } pd_params;
 
 /*
@@ -245,6 +264,27 @@ typedef struct {
  */
 pd_status pd_iterate(pd_plan* plan, pd_state* st, const pd_params* params, int32_t niter,
                      void* stream);
+
+/*
+ * One iteration split at its only exchange point, for a problem whose data blocks are
+ * spread over several GPUs (Sec. 3: the data blocks are processed in parallel and only
+ * sum_i G_i^T v_i travels back to the primal update). Each rank plans its own
+ * visibilities with the global block count (its other blocks hold no visibilities), so
+ * that the counter-based draws agree on every rank; the primal variables are
+ * replicated (every rank runs the same primal update).
+ * pd_iterate_dual: steps 3-14 (draws, F Z x~, degridding and the l2-ball update of this
+ * rank's active blocks, gridding of their dual change into the state's U, the sparsity
+ * dual update). The caller then sums U over the ranks (pd_state_u gives the device
+ * pointer of the state's U, complex [Kx/4][Ky][4] column panels, Kx*Ky elements; the
+ * sum must go to another buffer, since U keeps this rank's own part).
+ * pd_iterate_primal: steps 17-18 with the summed U (device, same layout; NULL = the
+ * state's own U). adaptive must be 0 (the residual norms would differ between ranks).
+ * Both asynchronous on `stream`; pd_iterate_dual + pd_iterate_primal(NULL) equals one
+ * iteration of pd_iterate. Errors: PD_EINVAL, PD_ECUDA.
+ */
+pd_status pd_iterate_dual(pd_plan* plan, pd_state* st, const pd_params* params, void* stream);
+pd_status pd_iterate_primal(pd_plan* plan, pd_state* st, const pd_params* params, const void* u, void* stream);
+pd_status pd_state_u(pd_state* st, void** u, int64_t* elements);
 
 /*
  * Per-phase kernel times accumulated by iterations run with params.profile = 1:

@@ -40,7 +40,7 @@ class PdParams(ctypes.Structure):
                 ("p_block", ctypes.c_void_p), ("p_basis", ctypes.c_void_p), ("adaptive", ctypes.c_int32),
                 ("adapt_n", ctypes.c_double), ("adapt_p_min", ctypes.c_double),
                 ("adapt_p_max", ctypes.c_double), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("adapt_exact", ctypes.c_int32)]
+                ("adapt_exact", ctypes.c_int32), ("per_block", ctypes.c_int32)]
 
 
 _lib = None
@@ -63,7 +63,11 @@ _SIGS = {
     "pd_state_create": ([_VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "pd_state_destroy": ([_VP], ctypes.c_int),
     "pd_state_set_data": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "pd_state_set_start": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "pd_iterate": ([_VP, _VP, ctypes.POINTER(PdParams), ctypes.c_int32, _VP], ctypes.c_int),
+    "pd_iterate_dual": ([_VP, _VP, ctypes.POINTER(PdParams), _VP], ctypes.c_int),
+    "pd_iterate_primal": ([_VP, _VP, ctypes.POINTER(PdParams), _VP, _VP], ctypes.c_int),
+    "pd_state_u": ([_VP, ctypes.POINTER(_VP), _VP], ctypes.c_int),
     "pd_state_get_x": ([_VP, _VP, _VP], ctypes.c_int),
     "pd_state_get_x_tilde": ([_VP, _VP, _VP], ctypes.c_int),
     "pd_state_get_s": ([_VP, _VP, _VP], ctypes.c_int),

@@ -162,15 +162,30 @@ class State:
             raise ValueError("eps must have one entry per block")
         B.call("pd_state_set_data", p.handle, self._h, _ptr(y), eps.ctypes.data, _stream())
 
+    def pd_state_set_start(self, x0=None, x_tilde0=None, s0=None, v0=None):
+        """Start values x^(0), x~^(0), s^(0), v^(0) (None = zero); call after pd_state_set_data."""
+        p = self.plan
+        args = []
+        for t, dt, shape, name in ((x0, p.real_dtype, (p.ny, p.nx), "x0"),
+                                   (x_tilde0, p.real_dtype, (p.ny, p.nx), "x_tilde0"),
+                                   (s0, p.real_dtype, (p.nbases, p.ny, p.nx), "s0"),
+                                   (v0, p.cplx_dtype, (p.nvis,), "v0")):
+            if t is None:
+                args.append(ctypes.c_void_p())
+            else:
+                _need(t, dt, shape, name)
+                args.append(_ptr(t))
+        B.call("pd_state_set_start", p.handle, self._h, *args, _stream())
+
     def pd_iterate(self, niter, tau, sigma, varsigma, kappa, psi_norm=1.0, seed=0, p_block=None, p_basis=None,
-                   adaptive=None, use_graph=False, profile=False):
+                   adaptive=None, use_graph=False, profile=False, per_block=False):
         p = self.plan
         pb = np.ascontiguousarray(np.ones(p.nblocks) if p_block is None else p_block, dtype=np.float64)
         ps = np.ascontiguousarray(np.ones(p.nbases) if p_basis is None else p_basis, dtype=np.float64)
         prm = B.PdParams(tau=tau, sigma=sigma, varsigma=varsigma, kappa=kappa, psi_norm=psi_norm, seed=int(seed),
                          p_block=pb.ctypes.data, p_basis=ps.ctypes.data, adaptive=0, adapt_n=0.0,
                          adapt_p_min=0.0, adapt_p_max=0.0, use_graph=int(bool(use_graph)),
-                         profile=int(bool(profile)))
+                         profile=int(bool(profile)), per_block=int(bool(per_block)))
         if adaptive is not None:
             prm.adaptive = 1
             prm.adapt_n = float(adaptive["n"])

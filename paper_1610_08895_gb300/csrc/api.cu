@@ -229,15 +229,13 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
             p->max_tile_segs = std::max(p->max_tile_segs, tile_seg_start[t + 1] - tile_seg_start[t]);
         if (p->max_tile_segs > 1024)
             return fail(PD_ENOTSUP, "more than 1024 blocks share one gridding tile; use a smaller tile");
-        // within each segment: by super-cell, then row-major by base cell (stable: ties keep
-        // user order); record the super-cell ranges of every segment
+        // within each segment: by 8 x 8 super-cell, then row-major by base cell (stable: ties
+        // keep user order), so that the points of one super-cell row are consecutive
         p->nsc_side = std::max(1, g.tile / SC);
-        const int nsc = p->nsc_side * p->nsc_side;
         auto scell_of = [&](int32_t m) {
             const int ly = by[m] & (g.tile - 1), lx = bx[m] & (g.tile - 1);
             return (ly / SC) * p->nsc_side + lx / SC;
         };
-        std::vector<int32_t> sc_start((size_t)p->nseg * (nsc + 1));
         for (int64_t sg = 0; sg < p->nseg; ++sg) {
             std::stable_sort(order.begin() + seg_start[sg], order.begin() + seg_start[sg + 1],
                              [&](int32_t a, int32_t b2) {
@@ -245,12 +243,6 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
                                  if (sa != sb) return sa < sb;
                                  return (by[a] != by[b2]) ? by[a] < by[b2] : bx[a] < bx[b2];
                              });
-            int32_t* o = &sc_start[(size_t)sg * (nsc + 1)];
-            int i = seg_start[sg];
-            for (int k = 0; k <= nsc; ++k) {
-                while (i < seg_start[sg + 1] && scell_of(order[i]) < k) ++i;
-                o[k] = i;
-            }
         }
         // segments of each block (tile order) for the fixed-order block reductions
         std::vector<int32_t> bss(p->d + 1, 0), bsl(p->nseg);
@@ -281,8 +273,6 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         ALLOC(p->block_seg_start, bss.size());
         ALLOC(p->block_seg_list, bsl.size());
         ALLOC(p->tile_order, tord.size());
-        ALLOC(p->seg_sc_start, sc_start.size());
-        CU(upload(p->seg_sc_start, sc_start));
         CU(upload(p->seg_start, seg_start));
         CU(upload(p->seg_block, seg_block));
         CU(upload(p->tile_seg_start, tile_seg_start));
@@ -354,8 +344,12 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
     // ---- scratch
     {
         const size_t K = (size_t)g.Kx * g.Ky, N = (size_t)g.nx * g.ny;
-        CU(dalloc_bytes(A, B, &p->t1, (size_t)g.Kx * g.ny * p->csz));
-        CU(dalloc_bytes(A, B, &p->gridb, K * p->csz));
+        // half-grid intermediates: column panels of the columns 0 .. nx (nx/4 + 1 panels)
+        const size_t half_cols = (size_t)(g.nx / 4 + 1) * 4;
+        CU(dalloc_bytes(A, B, &p->t1, half_cols * g.ny * p->csz));
+        CU(dalloc_bytes(A, B, &p->gridb, half_cols * g.Ky * p->csz));
+        CU(cudaMemset(p->t1, 0, half_cols * g.ny * p->csz));
+        CU(cudaMemset(p->gridb, 0, half_cols * g.Ky * p->csz));
         CU(dalloc_bytes(A, B, &p->gridu, K * p->csz));
         CU(dalloc_bytes(A, B, &p->rbuf, (size_t)M * p->csz));
         ALLOC(p->seg_part, 2 * std::max<int64_t>(p->nseg, 1));
@@ -587,6 +581,48 @@ extern "C" pd_status pd_state_set_data(pd_plan* p, pd_state* st, const void* y, 
     return PD_OK;
 }
 
+template <typename R>
+static pd_status set_start_t(pd_plan* p, pd_state* st, const void* x0, const void* xt0, const void* s0,
+                             const void* v0, cudaStream_t s) {
+    const size_t N = (size_t)p->g.nx * p->g.ny, K = (size_t)p->g.Kx * p->g.Ky;
+    if (x0) CU(cudaMemcpyAsync(st->x, x0, N * p->rsz, cudaMemcpyDeviceToDevice, s));
+    else CU(cudaMemsetAsync(st->x, 0, N * p->rsz, s));
+    if (xt0) CU(cudaMemcpyAsync(st->xt, xt0, N * p->rsz, cudaMemcpyDeviceToDevice, s));
+    else CU(cudaMemsetAsync(st->xt, 0, N * p->rsz, s));
+    if (s0) {
+        CU(cudaMemcpyAsync(st->s, s0, N * p->b * p->rsz, cudaMemcpyDeviceToDevice, s));
+        CU(psi_plain<R>(p, (const R*)st->s, (R*)st->st, s));                 // s~ = Psi s
+    } else {
+        CU(cudaMemsetAsync(st->s, 0, N * p->b * p->rsz, s));
+        CU(cudaMemsetAsync(st->st, 0, N * p->rsz, s));
+    }
+    if (v0) {
+        CU(gather_internal<R>(p, (const cplx_t<R>*)v0, (cplx_t<R>*)st->v, s));
+        CU(grid_plain<R>(p, (const cplx_t<R>*)v0, (cplx_t<R>*)st->u, s));   // U = G^T v
+    } else {
+        CU(cudaMemsetAsync(st->v, 0, p->M * p->csz, s));
+        CU(cudaMemsetAsync(st->u, 0, K * p->csz, s));
+    }
+    CU(cudaMemsetAsync(st->t, 0, sizeof(int64_t), s));
+    CU(cudaMemsetAsync(st->diag, 0, 2 * sizeof(double), s));
+    // residual norms of the adaptive probabilities: ||Phi_i x^(0) - y_i||
+    if (x0) {
+        CU(fwd_fft<R>(p, (const R*)st->x, (cplx_t<R>*)p->gridb, s));
+        CU(degrid_res_norms<R>(p, (const cplx_t<R>*)p->gridb, (const cplx_t<R>*)st->y, st->res_norm, s));
+    } else {
+        CU(init_res_norm(p, st, s));
+    }
+    CU(cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+extern "C" pd_status pd_state_set_start(pd_plan* p, pd_state* st, const void* x0, const void* x_tilde0,
+                                        const void* s0, const void* v0, void* stream) {
+    if (!p || !st || st->plan != p) return fail(PD_EINVAL, "pd_state_set_start: bad argument");
+    return p->prec == PD_F64 ? set_start_t<double>(p, st, x0, x_tilde0, s0, v0, (cudaStream_t)stream)
+                             : set_start_t<float>(p, st, x0, x_tilde0, s0, v0, (cudaStream_t)stream);
+}
+
 // One iteration of Algorithm 1 on stream s. With `concurrent`, the sparsity-prior
 // branch (steps 13-14: reads x~, writes s, s~ and the plan's wavelet scratch) runs on the
 // state's second stream between a fork after the draws and a join before the primal
@@ -601,9 +637,12 @@ static cudaError_t ensure_prior_stream(pd_state* st) {
     return cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming);
 }
 
+// Steps 3-14 of one iteration: draws, FZx~, degridding and the l2-ball dual update,
+// gridding of the dual change into the state's U, and the sparsity dual update with
+// s~ (on the second stream when `concurrent`). The join of the two branches is left
+// to the caller (enqueue_iteration waits for it before the primal update).
 template <typename R>
-static cudaError_t enqueue_iteration(pd_plan* p, pd_state* st, const pd_params* prm, cudaStream_t s,
-                                     bool concurrent = true) {
+static cudaError_t enqueue_dual(pd_plan* p, pd_state* st, const pd_params* prm, cudaStream_t s, bool concurrent) {
     cudaError_t e;
     SelectArgs sa{prm->seed, prm->adaptive, prm->adapt_n, prm->adapt_p_min, prm->adapt_p_max};
     if ((e = select_active(p, st, sa, s))) return e;
@@ -622,9 +661,15 @@ static cudaError_t enqueue_iteration(pd_plan* p, pd_state* st, const pd_params* 
     DualArgs da{st->y, st->v, st->block_active, st->eps, st->res_norm};
     if ((e = degrid_dual<R>(p, (const cplx_t<R>*)p->gridb, da, st->act_tiles, st->counts, s))) return e;
     if ((e = grid_dual<R>(p, da, st->act_tiles, st->counts, st->tile_active, (cplx_t<R>*)st->u, s))) return e;
-    if (concurrent && (e = cudaStreamWaitEvent(s, st->ev_join, 0))) return e;
+    return cudaSuccess;
+}
+
+// Steps 17-18 from the gridded dual sum u (the state's own U unless given).
+template <typename R>
+static cudaError_t enqueue_primal(pd_plan* p, pd_state* st, const pd_params* prm, const void* u, cudaStream_t s) {
+    cudaError_t e;
     PrimalArgs pa{prm->tau, prm->sigma, prm->varsigma, st->x, st->xt, st->st, st->prim_part};
-    if ((e = inv_fft<R>(p, (const cplx_t<R>*)st->u, nullptr, &pa, s))) return e;
+    if ((e = inv_fft<R>(p, (const cplx_t<R>*)(u ? u : st->u), nullptr, &pa, s))) return e;
     if ((e = primal_finish(p, st, s))) return e;
     if (prm->adaptive && prm->adapt_exact) {
         // Sec. 4: c_i of the next draw from ||Phi_i x^(t) - y_i|| of every block
@@ -633,6 +678,95 @@ static cudaError_t enqueue_iteration(pd_plan* p, pd_state* st, const pd_params* 
             return e;
     }
     return cudaSuccess;
+}
+
+template <typename R>
+static cudaError_t enqueue_iteration(pd_plan* p, pd_state* st, const pd_params* prm, cudaStream_t s,
+                                     bool concurrent = true) {
+    cudaError_t e;
+    if ((e = enqueue_dual<R>(p, st, prm, s, concurrent))) return e;
+    if (concurrent && (e = cudaStreamWaitEvent(s, st->ev_join, 0))) return e;
+    return enqueue_primal<R>(p, st, prm, nullptr, s);
+}
+
+// The plain per-block form of one iteration: the same steps as enqueue_iteration, with
+// the active sets drawn on the host (the same counter-based Philox draws) and one launch
+// of each data-fidelity operator per active block, one of each sparsity operator per
+// active basis. Resources are made on first use.
+static cudaError_t ensure_per_block(pd_plan* p, pd_state* st) {
+    if (st->pb_eye_blocks) return cudaSuccess;
+    const int d = p->d, b = p->b, nt = p->g.ntiles;
+    std::vector<int32_t> eyed((size_t)d * d, 0), eyeb((size_t)b * b, 0), flags((size_t)d * nt, 0);
+    for (int i = 0; i < d; ++i) eyed[(size_t)i * d + i] = 1;
+    for (int j = 0; j < b; ++j) eyeb[(size_t)j * b + j] = 1;
+    std::vector<std::vector<int32_t>> tl(d);
+    for (int t = 0; t < nt; ++t)
+        for (int sg = p->h_tile_seg_start[t]; sg < p->h_tile_seg_start[t + 1]; ++sg) {
+            const int blk = p->h_seg_block[sg];
+            tl[blk].push_back(t);
+            flags[(size_t)blk * nt + t] = 1;
+        }
+    std::vector<int32_t> tiles, counts((size_t)2 * d, 0);
+    st->h_pb_off.assign(d + 1, 0);
+    for (int i = 0; i < d; ++i) {
+        st->h_pb_off[i] = (int32_t)tiles.size();
+        tiles.insert(tiles.end(), tl[i].begin(), tl[i].end());
+        counts[2 * i + 1] = (int32_t)tl[i].size();
+    }
+    st->h_pb_off[d] = (int32_t)tiles.size();
+    cudaError_t e;
+    auto& A = st->allocs;
+    size_t& B = st->device_bytes;
+    if ((e = dalloc(A, B, &st->pb_eye_blocks, eyed.size())) || (e = dalloc(A, B, &st->pb_eye_bases, eyeb.size())) ||
+        (e = dalloc(A, B, &st->pb_tiles, std::max<size_t>(tiles.size(), 1))) ||
+        (e = dalloc(A, B, &st->pb_counts, counts.size())) || (e = dalloc(A, B, &st->pb_flags, flags.size())))
+        return e;
+    if ((e = upload(st->pb_eye_blocks, eyed)) || (e = upload(st->pb_eye_bases, eyeb)) ||
+        (e = upload(st->pb_tiles, tiles)) || (e = upload(st->pb_counts, counts)) || (e = upload(st->pb_flags, flags)))
+        return e;
+    st->h_act.assign(d, 0);
+    st->h_actb.assign(b, 0);
+    return cudaSuccess;
+}
+
+template <typename R>
+static cudaError_t enqueue_iteration_per_block(pd_plan* p, pd_state* st, const pd_params* prm, cudaStream_t s) {
+    cudaError_t e;
+    const int d = p->d, b = p->b;
+    const int64_t t = ++st->h_t;
+    for (int i = 0; i < d; ++i) st->h_act[i] = philox_uniform(prm->seed, (uint64_t)t, 0, i) < prm->p_block[i];
+    for (int j = 0; j < b; ++j) st->h_actb[j] = philox_uniform(prm->seed, (uint64_t)t, 1, j) < prm->p_basis[j];
+    // the state's copies of the draws and of t (read by pd_state_report); the host
+    // arrays stay untouched until the stream is synchronised at the end of the iteration
+    if ((e = cudaMemcpyAsync(st->block_active, st->h_act.data(), d * sizeof(int32_t), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(st->basis_active, st->h_actb.data(), b * sizeof(int32_t), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(st->t, &st->h_t, sizeof(int64_t), cudaMemcpyHostToDevice, s)))
+        return e;
+    if ((e = fwd_fft<R>(p, (const R*)st->xt, (cplx_t<R>*)p->gridb, s))) return e;
+    for (int i = 0; i < d; ++i) {
+        if (!st->h_act[i]) continue;
+        DualArgs da{st->y, st->v, st->pb_eye_blocks + (size_t)i * d, st->eps, st->res_norm};
+        if ((e = degrid_dual<R>(p, (const cplx_t<R>*)p->gridb, da, st->pb_tiles + st->h_pb_off[i],
+                                st->pb_counts + 2 * i, s)))
+            return e;
+    }
+    for (int i = 0; i < d; ++i) {
+        if (!st->h_act[i]) continue;
+        DualArgs da{st->y, st->v, st->pb_eye_blocks + (size_t)i * d, st->eps, st->res_norm};
+        if ((e = grid_dual<R>(p, da, st->pb_tiles + st->h_pb_off[i], st->pb_counts + 2 * i,
+                              st->pb_flags + (size_t)i * p->g.ntiles, (cplx_t<R>*)st->u, s)))
+            return e;
+    }
+    for (int j = 0; j < b; ++j) {
+        if (!st->h_actb[j]) continue;
+        if ((e = sparsity_dual<R>(p, (const R*)st->xt, (R*)st->s, (R*)st->st, st->pb_eye_bases + (size_t)j * b,
+                                  prm->kappa * prm->psi_norm, s)))
+            return e;
+    }
+    PrimalArgs pa{prm->tau, prm->sigma, prm->varsigma, st->x, st->xt, st->st, st->prim_part};
+    if ((e = inv_fft<R>(p, (const cplx_t<R>*)st->u, nullptr, &pa, s))) return e;
+    if ((e = primal_finish(p, st, s))) return e;
+    return cudaStreamSynchronize(s);
 }
 
 static std::vector<unsigned char> params_key(const pd_plan* p, const pd_params* prm, cudaStream_t s) {
@@ -651,6 +785,47 @@ static std::vector<unsigned char> params_key(const pd_plan* p, const pd_params* 
     return k;
 }
 
+static pd_status check_params(const pd_plan* p, const pd_params* prm) {
+    if (!prm->p_basis || (!prm->adaptive && !prm->p_block)) return fail(PD_EINVAL, "pd_iterate: missing probabilities");
+    for (int j = 0; j < p->b; ++j)
+        if (!(prm->p_basis[j] > 0 && prm->p_basis[j] <= 1)) return fail(PD_EINVAL, "p_basis must lie in (0, 1]");
+    if (!prm->adaptive) {
+        for (int i = 0; i < p->d; ++i)
+            if (!(prm->p_block[i] > 0 && prm->p_block[i] <= 1)) return fail(PD_EINVAL, "p_block must lie in (0, 1]");
+    }
+    return PD_OK;
+}
+
+extern "C" pd_status pd_iterate_dual(pd_plan* p, pd_state* st, const pd_params* prm, void* stream) {
+    if (!p || !st || !prm || st->plan != p) return fail(PD_EINVAL, "pd_iterate_dual: bad argument");
+    if (prm->adaptive) return fail(PD_EINVAL, "pd_iterate_dual: adaptive probabilities need every block's residual");
+    pd_status q = check_params(p, prm);
+    if (q != PD_OK) return q;
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaMemcpyAsync(st->p_block, prm->p_block, p->d * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(st->p_basis, prm->p_basis, p->b * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (p->prec == PD_F64) CU(enqueue_dual<double>(p, st, prm, s, true));
+    else CU(enqueue_dual<float>(p, st, prm, s, true));
+    CU(cudaStreamWaitEvent(s, st->ev_join, 0));
+    return PD_OK;
+}
+
+extern "C" pd_status pd_iterate_primal(pd_plan* p, pd_state* st, const pd_params* prm, const void* u, void* stream) {
+    if (!p || !st || !prm || st->plan != p) return fail(PD_EINVAL, "pd_iterate_primal: bad argument");
+    if (prm->adaptive) return fail(PD_EINVAL, "pd_iterate_primal: adaptive probabilities are not split");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->prec == PD_F64) CU(enqueue_primal<double>(p, st, prm, u, s));
+    else CU(enqueue_primal<float>(p, st, prm, u, s));
+    return PD_OK;
+}
+
+extern "C" pd_status pd_state_u(pd_state* st, void** u, int64_t* elements) {
+    if (!st || !u) return fail(PD_EINVAL, "pd_state_u: bad argument");
+    *u = st->u;
+    if (elements) *elements = (int64_t)st->plan->g.Kx * st->plan->g.Ky;
+    return PD_OK;
+}
+
 extern "C" pd_status pd_iterate(pd_plan* p, pd_state* st, const pd_params* prm, int32_t niter, void* stream) {
     if (!p || !st || !prm || st->plan != p || niter < 0) return fail(PD_EINVAL, "pd_iterate: bad argument");
     if (!prm->p_basis || (!prm->adaptive && !prm->p_block)) return fail(PD_EINVAL, "pd_iterate: missing probabilities");
@@ -665,10 +840,22 @@ extern "C" pd_status pd_iterate(pd_plan* p, pd_state* st, const pd_params* prm, 
               prm->adapt_p_min <= prm->adapt_p_max && prm->adapt_p_max <= 1 && prm->adapt_p_max >= nd))
             return fail(PD_EINVAL, "adaptive probabilities need 0 <= p_min <= n/d <= p_max <= 1");
     }
+    if (prm->per_block && (prm->adaptive || prm->use_graph || prm->profile))
+        return fail(PD_EINVAL, "pd_iterate: the per-block form needs adaptive = 0, use_graph = 0 and profile = 0");
     cudaStream_t s = (cudaStream_t)stream;
     if (!prm->adaptive) CU(cudaMemcpyAsync(st->p_block, prm->p_block, p->d * sizeof(double), cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(st->p_basis, prm->p_basis, p->b * sizeof(double), cudaMemcpyHostToDevice, s));
     if (niter == 0) return PD_OK;
+    if (prm->per_block) {
+        CU(ensure_per_block(p, st));
+        CU(cudaMemcpyAsync(&st->h_t, st->t, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        for (int k = 0; k < niter; ++k) {
+            if (p->prec == PD_F64) CU(enqueue_iteration_per_block<double>(p, st, prm, s));
+            else CU(enqueue_iteration_per_block<float>(p, st, prm, s));
+        }
+        return PD_OK;
+    }
     if (prm->use_graph) {
         // The caller's stream may be the legacy default stream, which cannot be captured:
         // capture and replay on the state's private stream, fenced by events both ways.

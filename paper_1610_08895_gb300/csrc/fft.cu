@@ -1,16 +1,21 @@
 // Oversampled 2-D FFT passes of Phi = G F Z and of its adjoint (Sec. 2), as
-// shared-memory Stockham transforms.
+// shared-memory Stockham transforms of compile-time length.
 //
 // The grid is (2 ny) x (2 nx) but only ny x nx of its input cells are non-zero
 // (zero padding by Z), and the adjoint only needs ny x nx of its outputs (the
 // crop of Z^T). Every pass therefore runs half-length transforms: with a length
 // 2n transform split into even and odd outputs (forward) or inputs (inverse),
 //   X[2j + r] = sum_l (x_l W_2n^{r l}) W_n^{j l},
-//   x_l       = E_l + W_2n^{-l} O_l,  E/O = inverse length-n transforms of even/odd inputs,
-// so each CTA transforms 2 x (columns it owns) sequences of length n in shared
-// memory. Layouts: images are row-major [ny][nx]; the row-pass intermediate t1
-// and the grids use column panels [K/4][rows][4] so that every column pass
-// reads and writes contiguous slabs.
+//   x_l       = E_l + W_2n^{-l} O_l,  E/O = inverse length-n transforms of even/odd inputs.
+// The image is real, so F Z x is Hermitian, B[-k] = conj(B[k]): the forward passes
+// produce only the columns kx = 0 .. nx (the "half grid"), transforming two image rows
+// at once as the real and imaginary parts of one complex row. The adjoint needs only
+// Re(Z^T F^H U) = Z^T F^H H with H the Hermitian part (U[k] + conj(U[-k])) / 2, whose
+// column transforms are again Hermitian in kx: the inverse column pass transforms the
+// columns kx = 0 .. nx of H and the inverse row pass two rows at once.
+// Layouts: images are row-major [ny][nx]; the half-grid intermediates (t1) and the
+// forward output use column panels [nx/4 + 1][rows][4]; the gridded U is the full
+// panel grid [Kx/4][Ky][4].
 #include "common.cuh"
 #include "plan.hpp"
 
@@ -60,278 +65,270 @@ template <int RAD> __host__ __device__ constexpr int bitrev(int k) {
     return r;
 }
 
-// One Stockham autosort stage of radix RAD over C = 2^logC interleaved sequences of
-// length L held in shared memory s[l * C + c]. Each of the `nwork` worker threads owns
-// E/RAD butterflies; values travel through registers, so the stage is in place. The
-// first stage (Ns = 1, every twiddle 1) can take its inputs straight from global
-// memory through ld(l, c) (GIN), and the last can hand its outputs to st(k, c, value,
-// active) instead of shared memory (GOUT). st is called by every thread of the CTA, so
-// it may exchange values between the lanes of a warp.
-// threadIdx.x read through a volatile move, so the index arithmetic derived from it is
-// redone per stage instead of being hoisted and held in registers across stages.
-__device__ __forceinline__ int tid_here() {
-    int t;
-    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
-    return t;
-}
+// Compile-time shape of the length-N transforms of one precision: each thread holds EPT
+// elements per stage (radix EPT stages after a first stage of the remaining radix), and
+// sequences are stored with one pad element per PADV elements against bank conflicts.
+template <typename R, int N> struct Shape {
+    static constexpr int RAD = sizeof(R) == 4 ? 16 : 8;
+    static constexpr int EPT = N < RAD ? N : RAD;
+    static constexpr int PADV = sizeof(R) == 4 ? 16 : 8;
+    static constexpr int PN = N + N / PADV;            // padded sequence length
+    static constexpr int first_radix() {
+        int r = N;
+        while (r > EPT) r /= EPT;
+        return r;
+    }
+};
+template <typename R> __device__ __forceinline__ int padi(int l) { return l + (l >> (sizeof(R) == 4 ? 4 : 3)); }
 
-template <typename R, int E, int RAD, int SIGN, bool GIN, bool GOUT, class Ld, class St>
-__device__ __forceinline__ void stockham_stage(cplx_t<R>* s, int L, int logC, int Ns, const cplx_t<R>* tw2L,
-                                               int nwork, const Ld& ld, const St& st) {
+// One Stockham autosort stage of radix RADS over NSEQ sequences of length N held in
+// shared memory (sequence c at s + c * PN, padded). NS is the product of the radices of
+// the earlier stages. Butterfly i (k = i mod NS) takes x[i + r N/RADS], multiplies by
+// W^{k r / (NS RADS)} (from twK[m] = exp(-2 pi i m / (2N)), conjugated for SIGN > 0),
+// transforms, and stores X_r at (i / NS) NS RADS + k + r NS. All reads happen before the
+// barrier, all writes after it, so the stage works in place.
+template <typename R, int N, int RADS, int NS, int SIGN, int NSEQ>
+__device__ __forceinline__ void stage(cplx_t<R>* s, const cplx_t<R>* __restrict__ twK) {
     using C2 = cplx_t<R>;
-    constexpr int JOBS = E / RAD;
-    const int tid = tid_here();
-    const bool act = tid < nwork;
-    const int LR = L / RAD;
-    const int Cm = (1 << logC) - 1;
-    const int twstep = (2 * L) / (Ns * RAD);
-    C2 v[JOBS][RAD];
+    using S = Shape<R, N>;
+    constexpr int NJ = N / RADS, JOBS = S::EPT / RADS, NT = N * NSEQ / S::EPT;
+    const bool act = NT >= 32 || (int)threadIdx.x < NT;     // CTAs are at least one warp
+    C2 v[JOBS][RADS];
 #pragma unroll
-    for (int i = 0; i < JOBS; ++i) {
-        const int q = tid + i * nwork;
-        const int c = q & Cm, j = q >> logC;
-        const int k = j & (Ns - 1);
+    for (int jb = 0; jb < JOBS; ++jb) {
+        const int job = act ? threadIdx.x + jb * NT : 0;
+        const int c = job / NJ, i = job % NJ, k = i % NS;
+        const C2* src = s + c * S::PN;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) {
-            C2 a = mk<C2>(R(0), R(0));
-            if (act) {
-                if (GIN) {
-                    a = ld(j + r * LR, c);
-                } else {
-                    a = s[((j + r * LR) << logC) + c];
-                    if (r > 0 && Ns > 1) {
-                        C2 w = tw2L[k * r * twstep];
-                        if (SIGN > 0) w.y = -w.y;
-                        a = cmul(a, w);
-                    }
-                }
+        for (int r = 0; r < RADS; ++r) {
+            C2 a = src[padi<R>(i + r * NJ)];
+            if (NS > 1 && r > 0) {
+                C2 w = __ldg(&twK[k * r * (2 * N / (NS * RADS))]);
+                if (SIGN > 0) w.y = -w.y;
+                a = cmul(a, w);
             }
-            v[i][r] = a;
+            v[jb][r] = a;
         }
-        dft_dif<RAD, SIGN>(v[i]);
+        dft_dif<RADS, SIGN>(v[jb]);
     }
-    if (!GIN && !GOUT) __syncthreads();
+    __syncthreads();
 #pragma unroll
-    for (int i = 0; i < JOBS; ++i) {
-        const int q = tid + i * nwork;
-        const int c = q & Cm, j = q >> logC;
-        const int k = j & (Ns - 1);
-        const int base = (j - k) * RAD + k;
+    for (int jb = 0; jb < JOBS; ++jb) {
+        if (!act) break;
+        const int job = threadIdx.x + jb * NT;
+        const int c = job / NJ, i = job % NJ, k = i % NS;
+        C2* dst = s + c * S::PN;
+        const int base = (i / NS) * NS * RADS + k;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) {
-            if (GOUT) st(base + r * Ns, c, v[i][bitrev<RAD>(r)], act);
-            else if (act) s[((base + r * Ns) << logC) + c] = v[i][bitrev<RAD>(r)];
-        }
+        for (int r = 0; r < RADS; ++r) dst[padi<R>(base + r * NS)] = v[jb][bitrev<RADS>(r)];
     }
-    if (!GOUT) __syncthreads();
+    __syncthreads();
 }
 
-template <typename R, int E, int RAD, int SIGN, bool GIN, bool GOUT, class Ld, class St>
-__device__ __forceinline__ void first_stage(cplx_t<R>* s, int L, int logC, const cplx_t<R>* tw2L, int nwork,
-                                            bool last, const Ld& ld, const St& st) {
-    if (GOUT && last) stockham_stage<R, E, RAD, SIGN, GIN, GOUT>(s, L, logC, 1, tw2L, nwork, ld, st);
-    else stockham_stage<R, E, RAD, SIGN, GIN, false>(s, L, logC, 1, tw2L, nwork, ld, st);
-}
-
-// C = 2^logC independent length-L DFTs (SIGN -1 forward, +1 inverse, unnormalised)
-// with tw2L[k] = exp(-2 pi i k / (2L)). Inputs come from ld when GIN, else from s in
-// natural order s[l * C + c]; outputs go to st when GOUT, else they are left in natural
-// order in s. The odd-sized radix runs first, where all its twiddles are 1.
-template <typename R, int E, int SIGN, bool GIN, bool GOUT, class Ld, class St>
-__device__ void fft_io(cplx_t<R>* s, int L, int logC, const cplx_t<R>* tw2L, const Ld& ld, const St& st) {
-    constexpr int LOGE = E >= 16 ? 4 : 3;
-    constexpr int RB = 1 << LOGE;
-    const int nwork = (L << logC) / E;
-    const int bits = 31 - __clz(L);
-    const int rem = bits % LOGE;
-    const int nst = bits / LOGE + (rem ? 1 : 0);
-    const bool last = nst == 1;
-    if (rem == 3) first_stage<R, E, 8, SIGN, GIN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
-    else if (rem == 2) first_stage<R, E, 4, SIGN, GIN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
-    else if (rem == 1) first_stage<R, E, 2, SIGN, GIN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
-    else first_stage<R, E, RB, SIGN, GIN, GOUT>(s, L, logC, tw2L, nwork, last, ld, st);
-    int Ns = rem ? 1 << rem : RB;
-    for (int b = nst - 1; b > 0; --b) {
-        if (GOUT && b == 1) stockham_stage<R, E, RB, SIGN, false, GOUT>(s, L, logC, Ns, tw2L, nwork, ld, st);
-        else stockham_stage<R, E, RB, SIGN, false, false>(s, L, logC, Ns, tw2L, nwork, ld, st);
-        Ns <<= LOGE;
+template <typename R, int N, int NS, int SIGN, int NSEQ>
+__device__ __forceinline__ void stages(cplx_t<R>* s, const cplx_t<R>* __restrict__ twK) {
+    if constexpr (NS < N) {
+        constexpr int RADS = NS == 1 ? Shape<R, N>::first_radix() : Shape<R, N>::EPT;
+        stage<R, N, RADS, NS, SIGN, NSEQ>(s, twK);
+        stages<R, N, NS * RADS, SIGN, NSEQ>(s, twK);
     }
 }
 
-template <typename R> struct FftE;
-template <> struct FftE<float> { static constexpr int value = 16; };
-template <> struct FftE<double> { static constexpr int value = 8; };
-
-template <typename C> __device__ __forceinline__ C shfl_xor(C v, int m) {
-    v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
-    v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
-    return v;
+// NSEQ unnormalised length-N DFTs (SIGN -1 forward, +1 inverse) of the sequences in s,
+// natural order in and out. Every thread of the CTA (N NSEQ / EPT of them) takes part.
+template <typename R, int N, int SIGN, int NSEQ>
+__device__ __forceinline__ void fft_smem(cplx_t<R>* s, const cplx_t<R>* __restrict__ twK) {
+    stages<R, N, 1, SIGN, NSEQ>(s, twK);
 }
+
+// Rows (pairs) per CTA of the row passes and columns per CTA of the column passes:
+// as many as keep a CTA at 512 threads (so a thread may hold 128 registers), at most 4,
+// at least 1 (the longest transforms then take 1024 threads).
+template <typename R, int N> struct PassShape {
+    static constexpr int EPT = Shape<R, N>::EPT;
+    static constexpr int FIT = 512 * EPT / (2 * N);
+    static constexpr int PAIRS = FIT < 1 ? 1 : (FIT > 4 ? 4 : FIT);
+    static constexpr int CQ = PAIRS;
+    static constexpr int NT_ROWS = 2 * PAIRS * N / EPT < 32 ? 32 : 2 * PAIRS * N / EPT;
+    static constexpr int NT_COLS = 2 * CQ * N / EPT < 32 ? 32 : 2 * CQ * N / EPT;
+    static constexpr size_t SMEM_ROWS = (size_t)2 * PAIRS * Shape<R, N>::PN * sizeof(cplx_t<R>);
+    static constexpr size_t SMEM_COLS = (size_t)2 * CQ * Shape<R, N>::PN * sizeof(cplx_t<R>);
+};
 
 // ---------------------------------------------------------------------------
-// Forward row pass (Z then F along x): RB image rows per CTA; smem column 2*rho + r
-// holds row rho pre-twiddled for the even (r = 0) or odd (r = 1) outputs.
-template <typename R>
-__global__ void __launch_bounds__(1024) k_fwd_rows(const R* __restrict__ x, cplx_t<R>* __restrict__ t1,
-                                                   const R* __restrict__ cx, const R* __restrict__ cy,
-                                                   const cplx_t<R>* __restrict__ twx, int nx, int ny, int RB) {
+// Forward row pass (Z, then F along x) of two image rows a = iy0 + 2 pr, b = a + 1 per
+// pair: z = Z x_a + i Z x_b. Sequence 2 pr holds z for the even outputs, 2 pr + 1 the
+// pre-twiddled z for the odd ones. Output: the half spectrum kx = 0 .. nx of each row,
+// X_a[k] = (Z[k] + conj Z[-k]) / 2 and X_b[k] = (Z[k] - conj Z[-k]) / (2i), into t1.
+template <typename R, int N>
+__global__ void __launch_bounds__(PassShape<R, N>::NT_ROWS) k_fwd_rows(
+    const R* __restrict__ x, cplx_t<R>* __restrict__ t1, const R* __restrict__ cx, const R* __restrict__ cy,
+    const cplx_t<R>* __restrict__ twx, int ny) {
     using C2 = cplx_t<R>;
+    using S = Shape<R, N>;
+    using P = PassShape<R, N>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* s = reinterpret_cast<C2*>(smraw);
-    const int logC = 31 - __clz(2 * RB), C = 2 * RB;
-    const int Kx = 2 * nx;
-    const int iy0 = blockIdx.x * RB;
-    for (int e = threadIdx.x; e < RB * nx; e += blockDim.x) {
-        const int rho = e / nx, ix = e - rho * nx;
-        const int iy = iy0 + rho;
-        const R val = x[(int64_t)iy * nx + ix] * cx[ix] * cy[iy];
-        const int lc = ix - nx / 2;
-        const int m = lc & (nx - 1);
-        const C2 w = twx[lc & (Kx - 1)];
-        s[m * C + 2 * rho] = mk<C2>(val, R(0));
-        s[m * C + 2 * rho + 1] = mk<C2>(val * w.x, val * w.y);
+    constexpr int NT = P::NT_ROWS, Kx = 2 * N;
+    const int iy0 = blockIdx.x * 2 * P::PAIRS;
+    for (int e = threadIdx.x; e < P::PAIRS * N; e += NT) {
+        const int pr = e / N, ix = e % N;
+        const int a = iy0 + 2 * pr;
+        const R c = cx[ix];
+        const R va = x[(int64_t)a * N + ix] * c * cy[a];
+        const R vb = x[(int64_t)(a + 1) * N + ix] * c * cy[a + 1];
+        const int lc = ix - N / 2;
+        const int m = padi<R>(lc & (N - 1));
+        const C2 w = __ldg(&twx[lc & (Kx - 1)]);
+        s[(2 * pr) * S::PN + m] = mk<C2>(va, vb);
+        s[(2 * pr + 1) * S::PN + m] = mk<C2>(va * w.x - vb * w.y, va * w.y + vb * w.x);
     }
     __syncthreads();
-    auto nl = [](int, int) { return mk<C2>(R(0), R(0)); };
-    auto ns = [](int, int, C2, bool) {};
-    fft_io<R, FftE<R>::value, -1, false, false>(s, nx, logC, twx, nl, ns);
-    for (int e = threadIdx.x; e < RB * Kx; e += blockDim.x) {
-        const int p = e / (4 * RB), rem = e - p * 4 * RB;
-        const int rho = rem >> 2, q = rem & 3;
-        const int kx = 4 * p + q;
-        t1[((int64_t)p * ny + iy0 + rho) * 4 + q] = s[(kx >> 1) * C + 2 * rho + (kx & 1)];
-    }
-}
-
-// Forward column pass (F along y): CQ columns of one panel per CTA; smem column
-// r * CQ + qq holds column qq pre-twiddled for output parity r.
-template <typename R>
-__global__ void __launch_bounds__(1024) k_fwd_cols(const cplx_t<R>* __restrict__ t1, cplx_t<R>* __restrict__ gb,
-                                                   const cplx_t<R>* __restrict__ twy, int ny, int CQ) {
-    using C2 = cplx_t<R>;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C2* s = reinterpret_cast<C2*>(smraw);
-    const int C = 2 * CQ, logC = 31 - __clz(C);
-    const int Ky = 2 * ny;
-    const int per = 4 / CQ;
-    const int p = blockIdx.x / per, q0 = (blockIdx.x - p * per) * CQ;
-    for (int e = threadIdx.x; e < ny * CQ; e += blockDim.x) {
-        const int iy = e / CQ, qq = e - iy * CQ;
-        const C2 val = t1[((int64_t)p * ny + iy) * 4 + q0 + qq];
-        const int lc = iy - ny / 2;
-        const int m = lc & (ny - 1);
-        s[m * C + qq] = val;
-        s[m * C + CQ + qq] = cmul(val, twy[lc & (Ky - 1)]);
-    }
-    __syncthreads();
-    auto nl = [](int, int) { return mk<C2>(R(0), R(0)); };
-    auto ns = [](int, int, C2, bool) {};
-    fft_io<R, FftE<R>::value, -1, false, false>(s, ny, logC, twy, nl, ns);
-    for (int e = threadIdx.x; e < Ky * CQ; e += blockDim.x) {
-        const int ky = e / CQ, qq = e - ky * CQ;
-        gb[((int64_t)p * Ky + ky) * 4 + q0 + qq] = s[(ky >> 1) * C + (ky & 1) * CQ + qq];
-    }
-}
-
-// Inverse column pass (F^H along y, crop to ny rows). Sequence c = r CQ + qq holds the
-// grid rows of parity r of column q0 + qq; the cropped row iy is
-// E[m] + conj(W_2ny^lc) O[m] with lc = iy - ny/2, m = lc mod ny. DIRECT: the odd
-// sequence's value comes from the lane CQ away and the row is stored from registers.
-template <typename R, bool DIRECT>
-__global__ void __launch_bounds__(1024) k_inv_cols(const cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ t1,
-                                                   const cplx_t<R>* __restrict__ twy, int ny, int CQ) {
-    using C2 = cplx_t<R>;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C2* s = reinterpret_cast<C2*>(smraw);
-    const int C = 2 * CQ, logC = 31 - __clz(C), lq = logC - 1;
-    const int Ky = 2 * ny, h = ny / 2;
-    const int per = 4 / CQ;
-    const int p = blockIdx.x / per, q0 = (blockIdx.x - p * per) * CQ;
-    const C2* src = U + ((int64_t)p * Ky << 2) + q0;
-    C2* dst = t1 + ((int64_t)p * ny << 2) + q0;
-    auto ld = [&](int m, int c) { return src[((2 * m + (c >> lq)) << 2) + (c & (CQ - 1))]; };
-    if (DIRECT) {
-        auto st = [&](int k, int c, C2 v, bool act) {
-            const C2 o = shfl_xor(v, CQ);
-            if (act && !(c >> lq)) {
-                const int lc = k < h ? k : k - ny;
-                dst[((lc + h) << 2) + c] = cadd(v, cmul(cconj(twy[lc & (Ky - 1)]), o));
-            }
-        };
-        fft_io<R, FftE<R>::value, +1, true, true>(s, ny, logC, twy, ld, st);
-    } else {
-        auto st = [](int, int, C2, bool) {};
-        fft_io<R, FftE<R>::value, +1, true, false>(s, ny, logC, twy, ld, st);
-        for (int e = threadIdx.x; e < ny * CQ; e += blockDim.x) {
-            const int iy = e / CQ, qq = e - iy * CQ;
-            const int lc = iy - h;
-            const int m = lc & (ny - 1);
-            const C2 w = cconj(twy[lc & (Ky - 1)]);
-            dst[(iy << 2) + qq] = cadd(s[m * C + qq], cmul(w, s[m * C + CQ + qq]));
+    fft_smem<R, N, -1, 2 * P::PAIRS>(s, twx);
+    // outputs ordered (panel, row, slot): 2 PAIRS rows x 4 slots of a panel are contiguous
+    constexpr int NPH = N / 4 + 1;
+    for (int e = threadIdx.x; e < NPH * 2 * P::PAIRS * 4; e += NT) {
+        const int q = e & 3, rr = (e >> 2) % (2 * P::PAIRS), pp = (e >> 2) / (2 * P::PAIRS);
+        const int kx = 4 * pp + q;
+        if (kx > N) continue;
+        const int pr = rr >> 1;
+        const C2* ev = s + (2 * pr) * S::PN;
+        const C2* od = ev + S::PN;
+        C2 z, zm;
+        if ((kx & 1) == 0) {
+            const int j = kx >> 1;
+            z = ev[padi<R>(j & (N - 1))];
+            zm = ev[padi<R>((N - j) & (N - 1))];
+        } else {
+            const int j = kx >> 1;
+            z = od[padi<R>(j)];
+            zm = od[padi<R>(N - 1 - j)];
         }
+        const C2 out = (rr & 1) ? mk<C2>(R(0.5) * (z.y + zm.y), R(0.5) * (zm.x - z.x))
+                                : mk<C2>(R(0.5) * (z.x + zm.x), R(0.5) * (z.y - zm.y));
+        t1[((int64_t)pp * ny + iy0 + rr) * 4 + q] = out;
     }
 }
 
-// Inverse row pass (F^H along x, crop, Re, deapodise), with either a plain store
-// (mode 0) or the primal update of Alg. 1 steps 17-18 as epilogue (mode 1). Sequence
-// c = 2 rho + r holds the grid columns of parity r of row iy0 + rho; DIRECT: the odd
-// sequence's value comes from the neighbouring lane.
-template <typename R, bool DIRECT>
-__global__ void __launch_bounds__(1024) k_inv_rows(const cplx_t<R>* __restrict__ t1, R* __restrict__ out,
-                                                   const R* __restrict__ cx, const R* __restrict__ cy,
-                                                   const cplx_t<R>* __restrict__ twx, int nx, int ny, int RB,
-                                                   int mode, R tau, R sigma, R varsigma, R* __restrict__ xs,
-                                                   R* __restrict__ xt, const R* __restrict__ st_,
-                                                   double* __restrict__ part) {
+// Forward column pass (F along y) of CQ half-grid columns of one panel: sequence qq holds
+// column q0 + qq for the even outputs, CQ + qq the pre-twiddled column for the odd ones.
+template <typename R, int N>
+__global__ void __launch_bounds__(PassShape<R, N>::NT_COLS) k_fwd_cols(
+    const cplx_t<R>* __restrict__ t1, cplx_t<R>* __restrict__ gb, const cplx_t<R>* __restrict__ twy) {
     using C2 = cplx_t<R>;
+    using S = Shape<R, N>;
+    using P = PassShape<R, N>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* s = reinterpret_cast<C2*>(smraw);
+    constexpr int NT = P::NT_COLS, CQ = P::CQ, Ky = 2 * N, PER = 4 / CQ;
+    const int p = blockIdx.x / PER, q0 = (blockIdx.x % PER) * CQ;
+    const C2* src = t1 + (int64_t)p * N * 4 + q0;
+    for (int e = threadIdx.x; e < N * CQ; e += NT) {
+        const int iy = e / CQ, qq = e % CQ;
+        const C2 val = src[iy * 4 + qq];
+        const int lc = iy - N / 2;
+        const int m = padi<R>(lc & (N - 1));
+        s[qq * S::PN + m] = val;
+        s[(CQ + qq) * S::PN + m] = cmul(val, __ldg(&twy[lc & (Ky - 1)]));
+    }
+    __syncthreads();
+    fft_smem<R, N, -1, 2 * CQ>(s, twy);
+    C2* dst = gb + (int64_t)p * Ky * 4 + q0;
+    for (int e = threadIdx.x; e < Ky * CQ; e += NT) {
+        const int ky = e / CQ, qq = e % CQ;
+        dst[ky * 4 + qq] = s[((ky & 1) * CQ + qq) * S::PN + padi<R>(ky >> 1)];
+    }
+}
+
+// Inverse column pass (F^H along y, crop to ny rows) of the Hermitian part of U for the
+// half-grid columns kx = 4 p + q0 + qq: h[ky] = (U[ky][kx] + conj U[-ky][-kx]) / 2, its
+// even inputs in sequence qq and odd inputs in CQ + qq; the cropped row iy is
+// E[m] + conj(W_2ny^lc) O[m] with lc = iy - ny/2, m = lc mod ny.
+template <typename R, int N>
+__global__ void __launch_bounds__(PassShape<R, N>::NT_COLS) k_inv_cols(
+    const cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ t1, const cplx_t<R>* __restrict__ twy, int Kx) {
+    using C2 = cplx_t<R>;
+    using S = Shape<R, N>;
+    using P = PassShape<R, N>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* s = reinterpret_cast<C2*>(smraw);
+    constexpr int NT = P::NT_COLS, CQ = P::CQ, Ky = 2 * N, PER = 4 / CQ;
+    const int p = blockIdx.x / PER, q0 = (blockIdx.x % PER) * CQ;
+    for (int e = threadIdx.x; e < Ky * CQ; e += NT) {
+        const int ky = e / CQ, qq = e % CQ;
+        const int kx = 4 * p + q0 + qq;
+        const int mkx = (Kx - kx) & (Kx - 1), mky = (Ky - ky) & (Ky - 1);
+        const C2 u = U[panel_off(ky, kx, Ky)], um = U[panel_off(mky, mkx, Ky)];
+        s[((ky & 1) * CQ + qq) * S::PN + padi<R>(ky >> 1)] =
+            mk<C2>(R(0.5) * (u.x + um.x), R(0.5) * (u.y - um.y));
+    }
+    __syncthreads();
+    fft_smem<R, N, +1, 2 * CQ>(s, twy);
+    C2* dst = t1 + (int64_t)p * N * 4 + q0;
+    for (int e = threadIdx.x; e < N * CQ; e += NT) {
+        const int iy = e / CQ, qq = e % CQ;
+        const int lc = iy - N / 2;
+        const int m = padi<R>(lc & (N - 1));
+        const C2 w = cconj(__ldg(&twy[lc & (Ky - 1)]));
+        dst[iy * 4 + qq] = cadd(s[qq * S::PN + m], cmul(w, s[(CQ + qq) * S::PN + m]));
+    }
+}
+
+// Inverse row pass (F^H along x of the Hermitian rows, crop, deapodise) of two rows at
+// once: Z[k] = T_a[k] + i T_b[k] with T[2nx - k] = conj T[k], so F^H Z = out_a + i out_b.
+// Mode 0 stores Re(Phi^H)-type output; mode 1 runs the primal update of Alg. 1 steps
+// 17-18 as epilogue with per-CTA FP64 partial norms.
+template <typename R, int N>
+__global__ void __launch_bounds__(PassShape<R, N>::NT_ROWS) k_inv_rows(
+    const cplx_t<R>* __restrict__ t1, R* __restrict__ out, const R* __restrict__ cx, const R* __restrict__ cy,
+    const cplx_t<R>* __restrict__ twx, int ny, int mode, R tau, R sigma, R varsigma, R* __restrict__ xs,
+    R* __restrict__ xt, const R* __restrict__ st_, double* __restrict__ part) {
+    using C2 = cplx_t<R>;
+    using S = Shape<R, N>;
+    using P = PassShape<R, N>;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[32];
     C2* s = reinterpret_cast<C2*>(smraw);
-    const int C = 2 * RB, logC = 31 - __clz(C);
-    const int Kx = 2 * nx, h = nx / 2;
-    const int iy0 = blockIdx.x * RB;
-    // per-thread partial sums of at most E terms in the working precision, then FP64
+    constexpr int NT = P::NT_ROWS, Kx = 2 * N, NPH = N / 4 + 1;
+    const int iy0 = blockIdx.x * 2 * P::PAIRS;
+    for (int e = threadIdx.x; e < NPH * P::PAIRS * 4; e += NT) {
+        const int q = e & 3, pr = (e >> 2) % P::PAIRS, pp = (e >> 2) / P::PAIRS;
+        const int k = 4 * pp + q;
+        if (k > N) continue;
+        const int a = iy0 + 2 * pr;
+        const C2 ta = t1[((int64_t)pp * ny + a) * 4 + q], tb = t1[((int64_t)pp * ny + a + 1) * 4 + q];
+        C2* seq = s + (2 * pr + (k & 1)) * S::PN;
+        seq[padi<R>(k >> 1)] = mk<C2>(ta.x - tb.y, ta.y + tb.x);
+        if (k != 0 && k != N) seq[padi<R>((Kx - k) >> 1)] = mk<C2>(ta.x + tb.y, tb.x - ta.y);
+    }
+    __syncthreads();
+    fft_smem<R, N, +1, 2 * P::PAIRS>(s, twx);
     R adx = R(0), ax = R(0);
-    auto finish = [&](int iy, int ix, R g0) {
-        const R g = g0 * cx[ix] * cy[iy];
-        const int64_t idx = (int64_t)iy * nx + ix;
-        if (mode == 0) {
-            out[idx] = g;
-        } else {
-            const R xo = xs[idx];
-            R xn = xo - tau * (sigma * st_[idx] + varsigma * g);
-            xn = xn > R(0) ? xn : R(0);
-            xt[idx] = R(2) * xn - xo;
-            xs[idx] = xn;
-            const R dd = xn - xo;
-            adx += dd * dd;
-            ax += xn * xn;
-        }
-    };
-    auto ld = [&](int m, int c) {
-        const int kx = 2 * m + (c & 1);
-        return t1[(((int64_t)(kx >> 2) * ny + iy0 + (c >> 1)) << 2) + (kx & 3)];
-    };
-    if (DIRECT) {
-        auto st = [&](int k, int c, C2 v, bool act) {
-            const C2 o = shfl_xor(v, 1);
-            if (act && !(c & 1)) {
-                const int lc = k < h ? k : k - nx;
-                const C2 w = cconj(twx[lc & (Kx - 1)]);
-                finish(iy0 + (c >> 1), lc + h, v.x + (w.x * o.x - w.y * o.y));
+    for (int e = threadIdx.x; e < P::PAIRS * N; e += NT) {
+        const int pr = e / N, ix = e % N;
+        const int lc = ix - N / 2;
+        const int m = padi<R>(lc & (N - 1));
+        const C2 w = cconj(__ldg(&twx[lc & (Kx - 1)]));
+        const C2* ev = s + (2 * pr) * S::PN;
+        const C2 z = cadd(ev[m], cmul(w, ev[S::PN + m]));
+        const R c = cx[ix];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int iy = iy0 + 2 * pr + h;
+            const R g = (h ? z.y : z.x) * c * cy[iy];
+            const int64_t idx = (int64_t)iy * N + ix;
+            if (mode == 0) {
+                out[idx] = g;
+            } else {
+                const R xo = xs[idx];
+                R xn = xo - tau * (sigma * st_[idx] + varsigma * g);
+                xn = xn > R(0) ? xn : R(0);
+                xt[idx] = R(2) * xn - xo;
+                xs[idx] = xn;
+                const R dd = xn - xo;
+                adx += dd * dd;
+                ax += xn * xn;
             }
-        };
-        fft_io<R, FftE<R>::value, +1, true, true>(s, nx, logC, twx, ld, st);
-    } else {
-        auto st = [](int, int, C2, bool) {};
-        fft_io<R, FftE<R>::value, +1, true, false>(s, nx, logC, twx, ld, st);
-        for (int e = threadIdx.x; e < RB * nx; e += blockDim.x) {
-            const int rho = e / nx, ix = e - rho * nx;
-            const int lc = ix - h;
-            const int m = lc & (nx - 1);
-            const C2 w = cconj(twx[lc & (Kx - 1)]);
-            const C2 ev = s[m * C + 2 * rho], od = s[m * C + 2 * rho + 1];
-            finish(iy0 + rho, ix, ev.x + (w.x * od.x - w.y * od.y));
         }
     }
     if (mode == 1) {
@@ -342,98 +339,106 @@ __global__ void __launch_bounds__(1024) k_inv_rows(const cplx_t<R>* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-struct PassCfg {
-    int rows_per_cta, cols_per_cta, threads_rows, threads_cols;
-    size_t smem_rows, smem_cols;
-    bool direct_rows, direct_cols;
-};
+// Launchers: one instantiation per transform length (image sides 16 .. 8192).
+#define PD_N_DISPATCH(n_, CALL)                                  \
+    switch (n_) {                                                \
+        case 16: { constexpr int NN = 16; CALL; } break;         \
+        case 32: { constexpr int NN = 32; CALL; } break;         \
+        case 64: { constexpr int NN = 64; CALL; } break;         \
+        case 128: { constexpr int NN = 128; CALL; } break;       \
+        case 256: { constexpr int NN = 256; CALL; } break;       \
+        case 512: { constexpr int NN = 512; CALL; } break;       \
+        case 1024: { constexpr int NN = 1024; CALL; } break;     \
+        case 2048: { constexpr int NN = 2048; CALL; } break;     \
+        case 4096: { constexpr int NN = 4096; CALL; } break;     \
+        case 8192: { if constexpr (sizeof(R) == 4) { constexpr int NN = 8192; CALL; } \
+                     else return cudaErrorInvalidValue; } break; \
+        default: return cudaErrorInvalidValue;                   \
+    }
 
-template <typename R> static PassCfg pass_cfg(const pd_plan* p) {
-    constexpr int E = FftE<R>::value;
-    const int nx = p->g.nx, ny = p->g.ny;
-    PassCfg c{};
-    // at most 512 threads and 100 KB of shared memory per CTA, so two CTAs share an SM
-    const int maxt = 512;
-    const size_t maxs = 100 * 1024;
-    int rb = 4;
-    while (rb > 1 && (nx * 2 * rb / E > maxt || (size_t)nx * 2 * rb * sizeof(cplx_t<R>) > maxs)) rb >>= 1;
-    int cq = 4;
-    while (cq > 1 && (ny * 2 * cq / E > maxt || (size_t)ny * 2 * cq * sizeof(cplx_t<R>) > maxs)) cq >>= 1;
-    if (rb > ny) rb = ny;
-    c.rows_per_cta = rb;
-    c.cols_per_cta = cq;
-    auto thr = [](int work) { int t = ((work + 31) / 32) * 32; return t < 32 ? 32 : t; };
-    c.threads_rows = thr(nx * 2 * rb / E);
-    c.threads_cols = thr(ny * 2 * cq / E);
-    c.smem_rows = (size_t)nx * 2 * rb * sizeof(cplx_t<R>);
-    c.smem_cols = (size_t)ny * 2 * cq * sizeof(cplx_t<R>);
-    // the register-level parity exchange of the inverse passes needs the partner
-    // sequence in a fixed neighbouring lane for every butterfly job
-    const int nw_rows = nx * 2 * rb / E, nw_cols = ny * 2 * cq / E;
-    c.direct_rows = nx * 2 * rb >= E && nw_rows % 2 == 0;
-    c.direct_cols = ny >= E && nw_cols % (2 * cq) == 0;
-    return c;
+template <typename R, int N>
+static cudaError_t launch_fwd_rows(const pd_plan* p, const R* x, cplx_t<R>* t1, cudaStream_t s) {
+    using P = PassShape<R, N>;
+    cudaError_t e;
+    if ((e = ensure_smem(k_fwd_rows<R, N>, P::SMEM_ROWS))) return e;
+    k_fwd_rows<R, N><<<p->g.ny / (2 * P::PAIRS), P::NT_ROWS, P::SMEM_ROWS, s>>>(
+        x, t1, (const R*)p->cx, (const R*)p->cy, (const cplx_t<R>*)p->twx, p->g.ny);
+    return cudaGetLastError();
+}
+template <typename R, int N>
+static cudaError_t launch_fwd_cols(const pd_plan* p, const cplx_t<R>* t1, cplx_t<R>* gb, cudaStream_t s) {
+    using P = PassShape<R, N>;
+    cudaError_t e;
+    if ((e = ensure_smem(k_fwd_cols<R, N>, P::SMEM_COLS))) return e;
+    k_fwd_cols<R, N><<<(p->g.nx / 4 + 1) * (4 / P::CQ), P::NT_COLS, P::SMEM_COLS, s>>>(
+        t1, gb, (const cplx_t<R>*)p->twy);
+    return cudaGetLastError();
+}
+template <typename R, int N>
+static cudaError_t launch_inv_cols(const pd_plan* p, const cplx_t<R>* U, cplx_t<R>* t1, cudaStream_t s) {
+    using P = PassShape<R, N>;
+    cudaError_t e;
+    if ((e = ensure_smem(k_inv_cols<R, N>, P::SMEM_COLS))) return e;
+    k_inv_cols<R, N><<<(p->g.nx / 4 + 1) * (4 / P::CQ), P::NT_COLS, P::SMEM_COLS, s>>>(
+        U, t1, (const cplx_t<R>*)p->twy, p->g.Kx);
+    return cudaGetLastError();
+}
+template <typename R, int N>
+static cudaError_t launch_inv_rows(const pd_plan* p, const cplx_t<R>* t1, R* out, const PrimalArgs* pa,
+                                   cudaStream_t s) {
+    using P = PassShape<R, N>;
+    cudaError_t e;
+    if ((e = ensure_smem(k_inv_rows<R, N>, P::SMEM_ROWS))) return e;
+    const int ctas = p->g.ny / (2 * P::PAIRS);
+    if (pa == nullptr)
+        k_inv_rows<R, N><<<ctas, P::NT_ROWS, P::SMEM_ROWS, s>>>(t1, out, (const R*)p->cx, (const R*)p->cy,
+                                                               (const cplx_t<R>*)p->twx, p->g.ny, 0, R(0), R(0),
+                                                               R(0), nullptr, nullptr, nullptr, nullptr);
+    else
+        k_inv_rows<R, N><<<ctas, P::NT_ROWS, P::SMEM_ROWS, s>>>(
+            t1, nullptr, (const R*)p->cx, (const R*)p->cy, (const cplx_t<R>*)p->twx, p->g.ny, 1, (R)pa->tau,
+            (R)pa->sigma, (R)pa->varsigma, (R*)pa->x, (R*)pa->xt, (const R*)pa->st, pa->part);
+    return cudaGetLastError();
 }
 
 int inv_rows_ctas(const pd_plan* p) {
-    PassCfg c = p->prec == PD_F64 ? pass_cfg<double>(p) : pass_cfg<float>(p);
-    return p->g.ny / c.rows_per_cta;
+    int pairs = 1;
+    auto get = [&](auto tag) {
+        using R = decltype(tag);
+        cudaError_t e = cudaSuccess;
+        PD_N_DISPATCH(p->g.nx, (pairs = PassShape<R, NN>::PAIRS));
+        return e;
+    };
+    if (p->prec == PD_F64) get(double{}); else get(float{});
+    return p->g.ny / (2 * pairs);
 }
 
 template <typename R>
 cudaError_t fwd_fft(const pd_plan* p, const R* x, cplx_t<R>* grid, cudaStream_t s) {
-    using C2 = cplx_t<R>;
-    const PassCfg c = pass_cfg<R>(p);
-    cudaError_t e;
-    if ((e = ensure_smem(k_fwd_rows<R>, c.smem_rows))) return e;
-    if ((e = ensure_smem(k_fwd_cols<R>, c.smem_cols))) return e;
-    const int nx = p->g.nx, ny = p->g.ny;
-    C2* t1 = (C2*)p->t1;
+    cudaError_t e = cudaSuccess;
+    cplx_t<R>* t1 = (cplx_t<R>*)p->t1;
     prof_mark(PH_FWD_ROWS, 0, s);
-    k_fwd_rows<R><<<ny / c.rows_per_cta, c.threads_rows, c.smem_rows, s>>>(
-        x, t1, (const R*)p->cx, (const R*)p->cy, (const C2*)p->twx, nx, ny, c.rows_per_cta);
+    PD_N_DISPATCH(p->g.nx, (e = launch_fwd_rows<R, NN>(p, x, t1, s)));
     prof_mark(PH_FWD_ROWS, 1, s);
+    if (e) return e;
     prof_mark(PH_FWD_COLS, 0, s);
-    k_fwd_cols<R><<<(p->g.Kx / 4) * (4 / c.cols_per_cta), c.threads_cols, c.smem_cols, s>>>(
-        t1, grid, (const C2*)p->twy, ny, c.cols_per_cta);
+    PD_N_DISPATCH(p->g.ny, (e = launch_fwd_cols<R, NN>(p, t1, grid, s)));
     prof_mark(PH_FWD_COLS, 1, s);
-    return cudaGetLastError();
-}
-
-template <typename R, bool DR, bool DC>
-static cudaError_t inv_fft_t(const pd_plan* p, const PassCfg& c, const cplx_t<R>* grid, R* out,
-                             const PrimalArgs* pa, cudaStream_t s) {
-    using C2 = cplx_t<R>;
-    cudaError_t e;
-    if ((e = ensure_smem(k_inv_cols<R, DC>, c.smem_cols))) return e;
-    if ((e = ensure_smem(k_inv_rows<R, DR>, c.smem_rows))) return e;
-    const int nx = p->g.nx, ny = p->g.ny;
-    C2* t1 = (C2*)p->t1;
-    prof_mark(PH_INV_COLS, 0, s);
-    k_inv_cols<R, DC><<<(p->g.Kx / 4) * (4 / c.cols_per_cta), c.threads_cols, c.smem_cols, s>>>(
-        grid, t1, (const C2*)p->twy, ny, c.cols_per_cta);
-    prof_mark(PH_INV_COLS, 1, s);
-    prof_mark(PH_INV_ROWS, 0, s);
-    if (pa == nullptr) {
-        k_inv_rows<R, DR><<<ny / c.rows_per_cta, c.threads_rows, c.smem_rows, s>>>(
-            t1, out, (const R*)p->cx, (const R*)p->cy, (const C2*)p->twx, nx, ny, c.rows_per_cta, 0, R(0), R(0),
-            R(0), nullptr, nullptr, nullptr, nullptr);
-    } else {
-        k_inv_rows<R, DR><<<ny / c.rows_per_cta, c.threads_rows, c.smem_rows, s>>>(
-            t1, nullptr, (const R*)p->cx, (const R*)p->cy, (const C2*)p->twx, nx, ny, c.rows_per_cta, 1,
-            (R)pa->tau, (R)pa->sigma, (R)pa->varsigma, (R*)pa->x, (R*)pa->xt, (const R*)pa->st, pa->part);
-    }
-    prof_mark(PH_INV_ROWS, 1, s);
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename R>
 cudaError_t inv_fft(const pd_plan* p, const cplx_t<R>* grid, R* out, const PrimalArgs* pa, cudaStream_t s) {
-    const PassCfg c = pass_cfg<R>(p);
-    if (c.direct_rows && c.direct_cols) return inv_fft_t<R, true, true>(p, c, grid, out, pa, s);
-    if (c.direct_rows) return inv_fft_t<R, true, false>(p, c, grid, out, pa, s);
-    if (c.direct_cols) return inv_fft_t<R, false, true>(p, c, grid, out, pa, s);
-    return inv_fft_t<R, false, false>(p, c, grid, out, pa, s);
+    cudaError_t e = cudaSuccess;
+    cplx_t<R>* t1 = (cplx_t<R>*)p->t1;
+    prof_mark(PH_INV_COLS, 0, s);
+    PD_N_DISPATCH(p->g.ny, (e = launch_inv_cols<R, NN>(p, grid, t1, s)));
+    prof_mark(PH_INV_COLS, 1, s);
+    if (e) return e;
+    prof_mark(PH_INV_ROWS, 0, s);
+    PD_N_DISPATCH(p->g.nx, (e = launch_inv_rows<R, NN>(p, t1, out, pa, s)));
+    prof_mark(PH_INV_ROWS, 1, s);
+    return e;
 }
 
 template cudaError_t fwd_fft<float>(const pd_plan*, const float*, float2*, cudaStream_t);

@@ -14,7 +14,8 @@
 //
 // Both directions work tile by tile (one CTA owns a T x T tile at a time) on the
 // tile plus a halo of J/2 - 1 cells before and J/2 after:
-// * degridding stages that window of the grid in shared memory and gathers from it;
+// * degridding stages that window of F Z x (held as its half grid: the columns
+//   kx <= nx, the others by conjugate symmetry) in shared memory and gathers from it;
 // * gridding accumulates the window in shared memory, adds the interior to U
 //   (nobody else writes it in that launch) and parks the halo ring; a second
 //   launch adds each tile's neighbours' rings to its border. No global atomics.
@@ -85,6 +86,15 @@ __device__ __forceinline__ void list_active_segments(int seg0, int nseg_t, const
     if (lane == 0) { act_pre[nact] = total; *nact_out = nact; }
 }
 
+// Cell (ky, kx) of F Z x from the half grid (columns 0 .. nx, column panels): the image
+// is real, so the columns kx > nx are conj(b[-ky][-kx]).
+template <typename C2>
+__device__ __forceinline__ C2 half_grid_at(const C2* __restrict__ gh, int ky, int kx, const Geo& g) {
+    if (kx <= g.nx) return gh[panel_off(ky, kx, g.Ky)];
+    const C2 v = gh[panel_off((g.Ky - ky) & (g.Ky - 1), g.Kx - kx, g.Ky)];
+    return mk<C2>(v.x, -v.y);
+}
+
 // ---------------------------------------------------------------- degridding
 // Warp-level segmented sum: the lanes with ok add (a, b) to their local segment ls;
 // lane 0 adds each segment's warp total into part[2 ls], part[2 ls + 1] (FP64 slots
@@ -144,7 +154,7 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
         for (int i = threadIdx.x; i < E * E; i += blockDim.x) {
             const int ey = i / E, ex = i - ey * E;
             const int ky = (oy - H + ey) & (g.Ky - 1), kx = (ox - H + ex) & (g.Kx - 1);
-            const C2 gv = grid[panel_off(ky, kx, g.Ky)];
+            const C2 gv = half_grid_at(grid, ky, kx, g);
             win[ey * EP + ex] = gv;
             if (PAIRS && ex > 0) win[E * EP + ey * EP + ex - 1] = gv;
         }
@@ -362,141 +372,244 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
     }
 }
 
-// J = 8 without atomics: the tile's 8 x 8 super-cells are processed in four colour
-// phases (row parity, column parity); in a phase the footprints of different
-// super-cells are disjoint, so each warp owns one super-cell at a time. Lane l owns
-// the cells whose (row mod 8, column mod 8) is (l / 4, 2 (l % 4) + {0, 1}): every
-// footprint holds exactly one cell of each class, so no other lane ever touches them.
-// A lane keeps the running sum of its current cell of each class in registers and
-// adds it to the shared accumulator (plain read-modify-write) only when the cell
-// changes; in the row-major order of a super-cell that is about once per 8 cells of
-// travel. Each warp first stages 32 visibilities (weights, value, footprint origin in
-// the window with the base cell's row and column mod 8), one per lane.
+// J <= 8 without atomics and without colour phases. Each warp of the CTA owns a private
+// accumulator window (the tile plus its halo) and takes chunks of 32
+// consecutive visibilities of the tile's active list; the CTA sums the windows at the
+// end of the tile. Cells are split into 64 classes by (window row mod 8, window column
+// mod 8); lane l owns classes (l / 4, 2 (l % 4) + {0, 1}). A J x J footprint (J <= 8)
+// holds at most one cell of each class, so the lanes of a warp never touch the same
+// cell. Visibilities arrive sorted by base cell inside 8 x 8 super-cells, so runs of
+// them share a "super-row" (one base-cell row, base columns g .. g + 7 with g = 0 mod 8):
+// over a super-row a class has one footprint row and two candidate columns (g + c and
+// g + c + 8), and the lane keeps one running sum per candidate cell in registers,
+// adding them to its window when the super-row changes.
+// Staging (one lane per visibility) writes per-class records that make the lane's work
+// a fixed-address read: for row class r the weight times the value, phi_y(tap) d; for
+// column class c the pair (weight if the class cell is the low candidate, weight if it
+// is the high one), one of them zero.
+constexpr int GW_WARPS = 4;
+constexpr int GW_RREC = 9;     // row records per staged point (8, padded against bank conflicts)
+constexpr int GW_CREC = 20;    // column record reals per staged point (16, padded, 16-byte rows)
+
+template <typename R> __device__ __forceinline__ void ld4(const R* p, R& a, R& b, R& c, R& d) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        a = q.x; b = q.y; c = q.z; d = q.w;
+    } else {
+        const double2 q0 = *reinterpret_cast<const double2*>(p), q1 = *reinterpret_cast<const double2*>(p + 2);
+        a = q0.x; b = q0.y; c = q1.x; d = q1.y;
+    }
+}
+// p[0] += a, p[1] += b (two adjacent complex cells, 16-byte aligned in FP32)
+template <typename C2> __device__ __forceinline__ void add2(C2* p, C2 a, C2 b) {
+    if constexpr (sizeof(C2) == 8) {
+        float4* q = reinterpret_cast<float4*>(p);
+        float4 t = *q;
+        t.x += a.x; t.y += a.y; t.z += b.x; t.w += b.y;
+        *q = t;
+    } else {
+        p[0] = cadd(p[0], a);
+        p[1] = cadd(p[1], b);
+    }
+}
+
+template <typename R>
+__host__ __device__ constexpr size_t grid8w_smem(int T, int ms) {
+    return (size_t)GW_WARPS * (T + 7) * (T + 8 > 16 ? T + 8 : 16) * 2 * sizeof(R)   // windows
+           + (size_t)GW_WARPS * 32 * (GW_RREC * 2 + GW_CREC) * sizeof(R)        // records
+           + (size_t)ms * sizeof(R)                                             // active segment scales
+           + (size_t)GW_WARPS * 32 * sizeof(int)                                // super-row keys
+           + (size_t)(3 * ms + 1) * sizeof(int);                                // active segment lists
+}
+
+// The raw inputs of one staged point, loaded a chunk ahead.
+template <typename R> struct GridIn {
+    cplx_t<R> a, b;     // MODE 1: r and v_old; MODE 0: the input value (a)
+    R fx, fy, sc;
+    int c, m;
+};
+
 template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k_grid8c(const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf,
-                                                cplx_t<R>* __restrict__ v, const R* __restrict__ scale,
-                                                const int32_t* __restrict__ active, const int32_t* __restrict__ cell,
-                                                const R* __restrict__ fxs, const R* __restrict__ fys,
-                                                const int32_t* __restrict__ perm,
-                                                const int32_t* __restrict__ seg_start,
-                                                const int32_t* __restrict__ seg_block,
-                                                const int32_t* __restrict__ tile_seg_start,
-                                                const int32_t* __restrict__ sc_start, int nsc_side,
-                                                const int32_t* __restrict__ list, const int32_t* __restrict__ count,
-                                                cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, int max_segs,
-                                                Geo g, R two_over_j, R beta, const KbPoly kp) {
+__device__ __forceinline__ void grid_load(GridIn<R>& in, int pos, int& j, const int* act_pre, const int* act_start,
+                                          const R* act_scale, const cplx_t<R>* __restrict__ src,
+                                          const cplx_t<R>* __restrict__ rbuf, const cplx_t<R>* __restrict__ v,
+                                          const int32_t* __restrict__ cell, const R* __restrict__ fxs,
+                                          const R* __restrict__ fys, const int32_t* __restrict__ perm) {
+    while (act_pre[j + 1] <= pos) ++j;
+    const int m = act_start[j] + pos - act_pre[j];
+    in.m = m;
+    in.fx = fxs[m];
+    in.fy = fys[m];
+    in.c = cell[m];
+    if (MODE == 1) {
+        in.a = rbuf[m];
+        in.b = v[m];
+        in.sc = act_scale[j];
+    } else {
+        in.a = src[perm[m]];
+    }
+}
+
+template <typename R, int J, int MODE>
+__global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
+    const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf, cplx_t<R>* __restrict__ v,
+    const R* __restrict__ scale, const int32_t* __restrict__ active, const int32_t* __restrict__ cell,
+    const R* __restrict__ fxs, const R* __restrict__ fys, const int32_t* __restrict__ perm,
+    const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_block,
+    const int32_t* __restrict__ tile_seg_start, const int32_t* __restrict__ list, const int32_t* __restrict__ count,
+    cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, int max_segs, Geo g, R two_over_j, R beta,
+    const KbPoly kp) {
+    static_assert(J <= 8 && J % 2 == 0, "class ownership needs J <= 8");
     using C2 = cplx_t<R>;
-    constexpr int J = 8;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2* acc = reinterpret_cast<C2*>(smraw);                  // [ext*ext] interleaved complex
-    int* act_seg = reinterpret_cast<int*>(acc + g.ext * g.ext);
-    int* act_pre = act_seg + max_segs;
-    __shared__ R sw[8][32][2 * J + 1];                       // per warp: wx[8], wy[8] of each staged point
-    __shared__ C2 sd[8][32];
-    __shared__ int scl[8][32];
-    __shared__ int next_sc, nact_s;
-    const int E = g.ext, EE = E * E;
+    // window rows T + 7 and pitch max(T + 8, 16): every class cell a lane can name (rows
+    // r0 .. r0 + 7, columns up to g + 15) lies inside its own warp's window, even where the
+    // footprint is narrower than 8 (J < 8) and the extra cells only ever receive zeros
+    const int T = g.tile, E = g.ext, EP = T + 8 > 16 ? T + 8 : 16, WS = (T + 7) * EP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int lcy = lane >> 2, lcx = (lane & 3) * 2;   // this lane's cell classes (mod 8)
-    const int nsc = nsc_side * nsc_side;
+    C2* wins = reinterpret_cast<C2*>(smraw);                               // [GW_WARPS][T + 7][EP]
+    C2* win = wins + (size_t)warp * WS;
+    C2* rrec_all = wins + (size_t)GW_WARPS * WS;                           // [GW_WARPS][32][GW_RREC]
+    R* crec_all = reinterpret_cast<R*>(rrec_all + GW_WARPS * 32 * GW_RREC); // [GW_WARPS][32][GW_CREC]
+    R* act_scale = crec_all + GW_WARPS * 32 * GW_CREC;                     // [max_segs]
+    int* skey_all = reinterpret_cast<int*>(act_scale + max_segs);          // [GW_WARPS][32]
+    int* act_seg = skey_all + GW_WARPS * 32;                               // [max_segs]
+    int* act_pre = act_seg + max_segs;                                     // [max_segs + 1]
+    int* act_start = act_pre + max_segs + 1;                               // [max_segs]
+    C2* rrec = rrec_all + warp * 32 * GW_RREC;
+    R* crec = crec_all + warp * 32 * GW_CREC;
+    int* skey = skey_all + warp * 32;
+    __shared__ int nact_s;
+    const int lcy = lane >> 2, lcx = (lane & 3) * 2;
     const int n = *count;
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int t = list[w];
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
-        const int oy = ty * g.tile, ox = tx * g.tile;
+        const int oy = ty * T, ox = tx * T;
         const int seg0 = tile_seg_start[t], nseg_t = tile_seg_start[t + 1] - seg0;
         list_active_segments(seg0, nseg_t, seg_block, MODE == 1 ? active : nullptr, seg_start, act_seg, act_pre,
                              &nact_s);
-        for (int i = threadIdx.x; i < EE; i += blockDim.x) acc[i] = mk<C2>(R(0), R(0));
-        for (int colour = 0; colour < 4; ++colour) {
-            const int py = colour >> 1, px = colour & 1;
-            const int hy = (nsc_side - py + 1) >> 1, hx = (nsc_side - px + 1) >> 1;
-            if (threadIdx.x == 0) next_sc = 0;
-            __syncthreads();
-            const int nact = nact_s;
-            for (;;) {
-                int k = 0;
-                if (lane == 0) k = atomicAdd(&next_sc, 1);
-                k = __shfl_sync(0xffffffffu, k, 0);
-                if (k >= hy * hx) break;
-                const int sc = (2 * (k / hx) + py) * nsc_side + 2 * (k % hx) + px;
-                int fill = 0;
-                // running sums of this lane's two cells (classes (lcy, lcx), (lcy, lcx + 1))
-                int key0 = -1, key1 = -1;
-                C2 r0 = mk<C2>(R(0), R(0)), r1 = mk<C2>(R(0), R(0));
-                for (int j = 0; j <= nact; ++j) {
-                    int pos = 0, end = 0;
-                    R scv = R(0);
-                    if (j < nact) {
-                        const int sg = act_seg[j];
-                        pos = sc_start[(int64_t)sg * (nsc + 1) + sc];
-                        end = sc_start[(int64_t)sg * (nsc + 1) + sc + 1];
-                        if (MODE == 1) scv = scale[seg_block[sg]];
-                    }
-                    // stage this range into the batch; process the batch when full (or at the end)
-                    while (pos < end || (j == nact && fill > 0)) {
-                        const int take = min(32 - fill, end - pos);
-                        if (take > 0 && lane >= fill && lane < fill + take) {
-                            const int m = pos + lane - fill;
-                            R wx[J], wy[J];
-                            kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
-                            kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
+        if (warp == 0) {
+            __syncwarp();
+            for (int k = lane; k < nact_s; k += 32) {
+                act_start[k] = seg_start[act_seg[k]];
+                if (MODE == 1) act_scale[k] = scale[seg_block[act_seg[k]]];
+            }
+        }
+        for (int i = lane; i < WS; i += 32) win[i] = mk<C2>(R(0), R(0));
+        __syncthreads();
+        const int total = act_pre[nact_s];
+        // chunks of 32 consecutive points, chunk k to warp k mod GW_WARPS (a fixed
+        // assignment, so the summation order and the result do not vary between runs)
+        const int nchunk = (total + 31) >> 5;
+        int j = 0;            // this lane's segment cursor (its positions only grow)
+        GridIn<R> in{};
+        int chunk = warp;
+        if (chunk < nchunk && chunk * 32 + lane < total)
+            grid_load<R, MODE>(in, chunk * 32 + lane, j, act_pre, act_start, act_scale, src, rbuf, v, cell, fxs, fys,
+                               perm);
+        for (; chunk < nchunk; chunk += GW_WARPS) {
+            const int fill = min(32, total - chunk * 32);
+            if (lane < fill) {
+                C2 d;
+                if (MODE == 1) {
+                    const C2 vn = cscale(in.a, in.sc);       // step 8: v_new = c_i r
+                    v[in.m] = vn;
+                    d = csub(vn, in.b);
+                } else {
+                    d = in.a;
+                }
+                R wx[J], wy[J];
+                kb_taps<R, J>(in.fx, wx, two_over_j, beta, kp);
+                kb_taps<R, J>(in.fy, wy, two_over_j, beta, kp);
+                const int r0 = (in.c >> 16) - oy, c0 = (in.c & 0xFFFF) - ox;   // footprint origin in the window
+                C2* rr = rrec + lane * GW_RREC;
 #pragma unroll
-                            for (int a = 0; a < J; ++a) { sw[warp][lane][a] = wx[a]; sw[warp][lane][J + a] = wy[a]; }
-                            sd[warp][lane] = grid_value<R, MODE>(m, src, rbuf, v, perm, scv);
-                            const int c = cell[m];
-                            const int bx = c & 0xFFFF, by = c >> 16;
-                            // footprint origin in the window, and the base cell's row and column mod 8
-                            scl[warp][lane] = (((by - oy) * E + (bx - ox)) << 6) | ((by & 7) << 3) | (bx & 7);
-                        }
-                        if (take > 0) { fill += take; pos += take; }
-                        if (fill < 32 && j < nact) break;
-                        __syncwarp();
-                        for (int q = 0; q < fill; ++q) {
-                            const int pk = scl[warp][q];
-                            const int b = (lcy - ((pk >> 3) & 7) + 3) & 7;
-                            const int a0 = (lcx - (pk & 7) + 3) & 7, a1 = (a0 + 1) & 7;
-                            const int rowk = (pk >> 6) + b * E;
-                            const int k0 = rowk + a0, k1 = rowk + a1;
-                            if (k0 != key0) {
-                                if (key0 >= 0) { C2 t0 = acc[key0]; t0.x += r0.x; t0.y += r0.y; acc[key0] = t0; }
-                                key0 = k0;
-                                r0 = mk<C2>(R(0), R(0));
-                            }
-                            if (k1 != key1) {
-                                if (key1 >= 0) { C2 t1 = acc[key1]; t1.x += r1.x; t1.y += r1.y; acc[key1] = t1; }
-                                key1 = k1;
-                                r1 = mk<C2>(R(0), R(0));
-                            }
-                            const R wy = sw[warp][q][J + b];
-                            const R w0 = sw[warp][q][a0] * wy, w1 = sw[warp][q][a1] * wy;
-                            const C2 d = sd[warp][q];
-                            r0.x += w0 * d.x; r0.y += w0 * d.y;
-                            r1.x += w1 * d.x; r1.y += w1 * d.y;
-                        }
-                        __syncwarp();
-                        fill = 0;
+                for (int b = 0; b < 8; ++b) {
+                    const R wv = b < J ? wy[b] : R(0);
+                    rr[(r0 + b) & 7] = mk<C2>(wv * d.x, wv * d.y);
+                }
+                const int gam = c0 & 7;
+                R* cr = crec + lane * GW_CREC;
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const R wv = a < J ? wx[a] : R(0);
+                    const int sidx = gam + a;                           // column offset from g
+                    *reinterpret_cast<C2*>(cr + 2 * (sidx & 7)) = sidx >= 8 ? mk<C2>(R(0), wv) : mk<C2>(wv, R(0));
+                }
+                skey[lane] = (r0 << 16) | (c0 & ~7);
+            }
+            // the next chunk's loads go out now and land while this one is accumulated
+            const int nxt = chunk + GW_WARPS;
+            if (nxt < nchunk && nxt * 32 + lane < total)
+                grid_load<R, MODE>(in, nxt * 32 + lane, j, act_pre, act_start, act_scale, src, rbuf, v, cell, fxs,
+                                   fys, perm);
+            __syncwarp();
+            int cur = -1;
+            C2 lo0 = mk<C2>(R(0), R(0)), hi0 = lo0, lo1 = lo0, hi1 = lo0;
+#pragma unroll 2
+            for (int q = 0; q < fill; ++q) {
+                const int key = skey[q];
+                const C2 ry = rrec[q * GW_RREC + lcy];
+                R wl0, wh0, wl1, wh1;
+                ld4(crec + q * GW_CREC + 2 * lcx, wl0, wh0, wl1, wh1);
+                if (key != cur) {                                       // warp-uniform
+                    if (cur >= 0) {
+                        const int r0 = cur >> 16, g0 = cur & 0xFFFF;
+                        C2* cp = win + (r0 + ((lcy - r0) & 7)) * EP + g0 + lcx;
+                        add2(cp, lo0, lo1);
+                        add2(cp + 8, hi0, hi1);
+                        lo0 = hi0 = lo1 = hi1 = mk<C2>(R(0), R(0));
+                    }
+                    cur = key;
+                }
+                lo0.x += wl0 * ry.x; lo0.y += wl0 * ry.y;
+                hi0.x += wh0 * ry.x; hi0.y += wh0 * ry.y;
+                lo1.x += wl1 * ry.x; lo1.y += wl1 * ry.y;
+                hi1.x += wh1 * ry.x; hi1.y += wh1 * ry.y;
+            }
+            if (cur >= 0) {
+                const int r0 = cur >> 16, g0 = cur & 0xFFFF;
+                C2* cp = win + (r0 + ((lcy - r0) & 7)) * EP + g0 + lcx;
+                add2(cp, lo0, lo1);
+                add2(cp + 8, hi0, hi1);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        // sum of the warps' windows: interior into U, halo ring into the ring slot; the U
+        // reads of a batch of cells go out together
+        const int H = g.halo_lo;
+        C2* rg = ring + (int64_t)t * g.ring;
+        constexpr int EB = 8;
+        for (int i0 = threadIdx.x; i0 < E * E; i0 += EB * (int)blockDim.x) {
+            C2 uo[EB];
+            int64_t off[EB];
+#pragma unroll
+            for (int k = 0; k < EB; ++k) {
+                const int i = i0 + k * (int)blockDim.x;
+                off[k] = -1;
+                uo[k] = mk<C2>(R(0), R(0));
+                if (i < E * E) {
+                    const int ey = i / E, ex = i - ey * E;
+                    if (ey >= H && ey < H + T && ex >= H && ex < H + T) {
+                        off[k] = panel_off(oy + ey - H, ox + ex - H, g.Ky);
+                        if (MODE == 1) uo[k] = U[off[k]];
                     }
                 }
-                if (key0 >= 0) { C2 t0 = acc[key0]; t0.x += r0.x; t0.y += r0.y; acc[key0] = t0; }
-                if (key1 >= 0) { C2 t1 = acc[key1]; t1.x += r1.x; t1.y += r1.y; acc[key1] = t1; }
             }
-            __syncthreads();
-        }
-        // interior into U, halo ring into the ring slot
-        const int H = g.halo_lo, T = g.tile;
-        for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-            const int iy = i / T, ix = i - iy * T;
-            const int64_t off = panel_off(oy + iy, ox + ix, g.Ky);
-            C2 val = acc[(iy + H) * E + ix + H];
-            if (MODE == 1) val = cadd(U[off], val);
-            U[off] = val;
-        }
-        C2* rg = ring + (int64_t)t * g.ring;
-        for (int i = threadIdx.x; i < EE; i += blockDim.x) {
-            const int ey = i / E, ex = i - ey * E;
-            if (ey >= H && ey < H + T && ex >= H && ex < H + T) continue;
-            rg[ring_index(ey, ex, g)] = acc[i];
+#pragma unroll
+            for (int k = 0; k < EB; ++k) {
+                const int i = i0 + k * (int)blockDim.x;
+                if (i >= E * E) break;
+                const int ey = i / E, ex = i - ey * E;
+                const int kk = ey * EP + ex;
+                C2 sum = wins[kk];
+#pragma unroll
+                for (int ww = 1; ww < GW_WARPS; ++ww) sum = cadd(sum, wins[(size_t)ww * WS + kk]);
+                if (off[k] >= 0) U[off[k]] = cadd(uo[k], sum);
+                else rg[ring_index(ey, ex, g)] = sum;
+            }
         }
         __syncthreads();
     }
@@ -644,17 +757,18 @@ static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const D
     cplx_t<R>* vv = a ? (cplx_t<R>*)a->v : nullptr;
     const int32_t* act = a ? a->block_active : nullptr;
     cudaError_t e;
-    if constexpr (J == 8) {
-        const size_t smem8 = (size_t)g.ext * g.ext * sizeof(cplx_t<R>) + lists;
-        if ((e = ensure_smem(k_grid8c<R, MODE>, smem8))) return e;
-        // one warp per super-cell of a colour phase: 4 warps for 32-cell tiles, 8 above
-        const int threads = p->nsc_side <= 4 ? 128 : 256;
-        const int ctas8 = std::min(g.ntiles, p->num_sms * (threads == 128 ? 12 : 4));
-        k_grid8c<R, MODE><<<ctas8, threads, smem8, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell,
-                                                  (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start,
-                                                  p->seg_block, p->tile_seg_start, p->seg_sc_start, p->nsc_side,
-                                                  tiles, count, U, (cplx_t<R>*)p->ringbuf, ms, g, toj, beta,
-                                                  p->kbpoly);
+    if constexpr (J <= 8) {
+        const size_t smem8 = grid8w_smem<R>(g.tile, ms);
+        if ((e = ensure_smem(k_grid8w<R, J, MODE>, smem8))) return e;
+        int per_sm = 0;
+        int ctas8 = std::min(g.ntiles, p->num_sms * 8);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid8w<R, J, MODE>, GW_WARPS * 32, smem8) ==
+                cudaSuccess && per_sm > 0)
+            ctas8 = std::min(ctas8, per_sm * p->num_sms);
+        k_grid8w<R, J, MODE><<<ctas8, GW_WARPS * 32, smem8, s>>>(
+            src, rb, vv, (const R*)p->blk_scale, act, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm,
+            p->seg_start, p->seg_block, p->tile_seg_start, tiles, count, U, (cplx_t<R>*)p->ringbuf, ms, g, toj,
+            beta, p->kbpoly);
     } else {
         const size_t smem = (size_t)2 * g.ext * g.ext * sizeof(R) + lists;
         if ((e = ensure_smem(k_grid<R, J, MODE>, smem))) return e;

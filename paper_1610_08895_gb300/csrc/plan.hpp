@@ -36,9 +36,8 @@ struct KbPoly {
     float c[16][KB_DEG + 1];
 };
 
-// Super-cells of SC x SC base cells inside a tile; two super-cells of the same
-// colour (row and column parity) are >= SC apart, so for J <= SC + 1 the J x J
-// footprints of their visibilities never overlap.
+// Super-cells of SC x SC base cells inside a tile: the visibilities of a segment are
+// sorted by super-cell, then row-major by base cell (the gridding's super-rows).
 constexpr int SC = 8;
 
 // Element offset of grid cell (ky, kx) in the column-panel layout [Kx/PW][K][PW].
@@ -72,7 +71,6 @@ struct pd_plan {
     int32_t* seg_start = nullptr;  // [nseg + 1]
     int32_t* seg_block = nullptr;  // [nseg]
     int32_t* tile_seg_start = nullptr;  // [ntiles + 1]
-    int32_t* seg_sc_start = nullptr;       // [nseg][nsc + 1]: super-cell ranges inside each segment
     int nsc_side = 0;                      // super-cells per tile side (tile / SC)
     int max_tile_segs = 0;                 // most (tile, block) segments in one tile
     pdgb::KbPoly kbpoly{};
@@ -94,8 +92,8 @@ struct pd_plan {
     std::vector<int> h_filt_len;
 
     // scratch
-    void* t1 = nullptr;            // complex [Kx/PW][ny][PW] row-pass intermediate
-    void* gridb = nullptr;         // complex [Kx/PW][Ky][PW] b~ = F Z x~
+    void* t1 = nullptr;            // complex [nx/PW + 1][ny][PW] half-spectrum row-pass intermediate
+    void* gridb = nullptr;         // complex [nx/PW + 1][Ky][PW] b~ = F Z x~, columns 0 .. nx
     void* gridu = nullptr;         // complex grid for the plain adjoint
     void* rbuf = nullptr;          // complex [M] residuals r = v + G b - y (internal order)
     double* seg_part = nullptr;    // [2 * nseg] per-segment FP64 partial norms
@@ -144,6 +142,15 @@ struct pd_state {
     // run concurrently with the data-fidelity steps 6-11), with its fork/join events
     cudaStream_t pstream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // plain per-block form (pd_params.per_block): one-hot activity flags, each block's tiles
+    int32_t* pb_eye_blocks = nullptr;  // [d][d]
+    int32_t* pb_eye_bases = nullptr;   // [b][b]
+    int32_t* pb_tiles = nullptr;       // tiles of block i at pb_tiles[h_pb_off[i] ...]
+    int32_t* pb_counts = nullptr;      // [d][2]: {0, number of tiles of block i}
+    int32_t* pb_flags = nullptr;       // [d][ntiles]: tile holds block i
+    std::vector<int32_t> h_pb_off;
+    std::vector<int32_t> h_act, h_actb;
+    int64_t h_t = 0;
     // per-phase timing (pd_params.profile)
     cudaEvent_t prof_ev[2 * 12] = {};
     double prof_ms[12] = {};

@@ -140,3 +140,28 @@ def test_adaptive_probabilities_exact_reading(use_graph):
     assert rel(st.x().cpu().numpy(), st_ref.x) < TOL_IT32
     assert np.allclose(rep["res_norm"], st_ref.res_norm, rtol=1e-4)
     assert rep["p_block"].sum() == pytest.approx(4.0, rel=1e-9)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_per_block_form_matches_batched_form_and_oracle(precision):
+    # one launch per active block per operator (host draws) against the batched form and
+    # the oracle: same draws, same iterates up to the rounding order
+    prob, _ = make_problem(64, 8192, 16, 8, (0, 1, 2), 2, uv_kind="radial", blocks="annuli", nannuli=16)
+    kw = _steps(prob)
+    args = dict(seed=5, p_block=[0.5] * 16, p_basis=[0.5] * 3, **kw)
+    niter = 20
+    st_ref, draws = PD.pd_run(prob, niter, **args)
+    plan, st = _setup(prob, precision)
+    st.pd_iterate(niter, per_block=True, **args)
+    rep = st.report()
+    assert rep["t"] == niter
+    assert list(rep["block_active"]) == list(draws[-1][0])
+    assert list(rep["basis_active"]) == list(draws[-1][1])
+    x_pb = st.x().cpu().numpy()
+    plan2, st2 = _setup(prob, precision)
+    st2.pd_iterate(niter, **args)
+    x_b = st2.x().cpu().numpy()
+    tol_it = TOL_IT64 if precision == "f64" else TOL_IT32
+    assert rel(x_pb, st_ref.x) < tol_it
+    assert rel(st.v().cpu().numpy(), st_ref.v) < tol_it
+    assert rel(x_pb, x_b) < (1e-12 if precision == "f64" else 1e-5)
