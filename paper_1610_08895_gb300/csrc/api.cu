@@ -146,15 +146,15 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
     g.nx = d->nx; g.ny = d->ny; g.Kx = 2 * d->nx; g.Ky = 2 * d->ny;
     g.J = d->kernel_width;
     g.beta = d->kb_beta > 0 ? d->kb_beta : kb_beta_default(g.J);
-    // default tile: 32 cells (the densest tiles bound the gridding critical path)
+    // default tile: 32 cells (the densest tiles bound the gridding critical path); at least
+    // two tiles per grid side, for the colour classes of the gridding
     int T = d->tile ? d->tile : 32;
-    while (T > std::min(g.Kx, g.Ky)) T >>= 1;
+    while (T > std::min(g.Kx, g.Ky) / 2) T >>= 1;
     while (T < g.J) T <<= 1;
-    if (T > std::min(g.Kx, g.Ky)) return fail(PD_ENOTSUP, "grid smaller than the kernel width");
+    if (T > std::min(g.Kx, g.Ky) / 2) return fail(PD_ENOTSUP, "grid side below twice the kernel width");
     g.tile = T; g.logT = ilog2(T);
     g.ntx = g.Kx / T; g.nty = g.Ky / T; g.ntiles = g.ntx * g.nty;
     g.ext = T + g.J - 1; g.halo_lo = g.J / 2 - 1; g.halo_hi = g.J / 2;
-    g.ring = (g.J - 1) * (g.ext + T);
     p->M = d->nvis; p->d = d->nblocks; p->b = d->nbases; p->L = d->levels;
     p->basis_ids.assign(d->basis_ids, d->basis_ids + d->nbases);
     p->n_wavelet = 0;
@@ -273,6 +273,19 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         ALLOC(p->block_seg_start, bss.size());
         ALLOC(p->block_seg_list, bsl.size());
         ALLOC(p->tile_order, tord.size());
+        {
+            // tiles of each colour in heaviest-first order
+            const int q = g.ntiles / 4;
+            std::vector<int32_t> col((size_t)g.ntiles), fill(4, 0), cc(4, q);
+            for (int k = 0; k < g.ntiles; ++k) {
+                const int c = tile_colour(tord[k], g.ntx);
+                col[(size_t)c * q + fill[c]++] = tord[k];
+            }
+            ALLOC(p->colour_tiles, col.size());
+            ALLOC(p->colour_counts, 4);
+            CU(upload(p->colour_tiles, col));
+            CU(upload(p->colour_counts, cc));
+        }
         CU(upload(p->seg_start, seg_start));
         CU(upload(p->seg_block, seg_block));
         CU(upload(p->tile_seg_start, tile_seg_start));
@@ -302,15 +315,13 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
     }
     {
         std::vector<int32_t> counts = {(int32_t)p->nseg, g.ntiles};
-        std::vector<int32_t> ob(p->d, 1), obs(p->b, 1), ot(g.ntiles, 1);
+        std::vector<int32_t> ob(p->d, 1), obs(p->b, 1);
         ALLOC(p->counts_all, 2);
         ALLOC(p->ones_block, ob.size());
         ALLOC(p->ones_basis, obs.size());
-        ALLOC(p->tile_ones, ot.size());
         CU(upload(p->counts_all, counts));
         CU(upload(p->ones_block, ob));
         CU(upload(p->ones_basis, obs));
-        CU(upload(p->tile_ones, ot));
     }
     // ---- tables
     {
@@ -355,13 +366,14 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         ALLOC(p->seg_part, 2 * std::max<int64_t>(p->nseg, 1));
         ALLOC(p->blk_norm, 2 * p->d);
         CU(dalloc_bytes(A, B, &p->blk_scale, p->d * p->rsz));
-        CU(dalloc_bytes(A, B, &p->ringbuf, (size_t)g.ntiles * g.ring * p->csz));
         const size_t llsz = (size_t)p->b * (g.ny / 2) * (g.nx / 2) * p->rsz;
         CU(dalloc_bytes(A, B, &p->ll[0], llsz));
         CU(dalloc_bytes(A, B, &p->ll[1], llsz));
         CU(dalloc_bytes(A, B, &p->ds, (size_t)p->b * N * p->rsz));
+        CU(dalloc_bytes(A, B, &p->synpart, (size_t)p->b * N * p->rsz));
         p->red_len = 1024;
         ALLOC(p->red, p->red_len + 8);
+        ALLOC(p->sched, 8);
         CU(cudaMemset(p->ds, 0, (size_t)p->b * N * p->rsz));
     }
 #undef ALLOC
@@ -537,7 +549,7 @@ extern "C" pd_status pd_state_create(pd_plan* p, pd_state** out) {
               !dalloc(A, B, &st->p_basis, p->b) && !dalloc(A, B, &st->block_active, p->d) &&
               !dalloc(A, B, &st->basis_active, p->b) &&
               !dalloc(A, B, &st->act_tiles, p->g.ntiles) && !dalloc(A, B, &st->tile_active, p->g.ntiles) &&
-              !dalloc(A, B, &st->counts, 2) && !dalloc(A, B, &st->t, 1) && !dalloc(A, B, &st->diag, 2) &&
+              !dalloc(A, B, &st->act_col, p->g.ntiles) && !dalloc(A, B, &st->counts, 6) && !dalloc(A, B, &st->t, 1) && !dalloc(A, B, &st->diag, 2) &&
               !dalloc(A, B, &st->prim_part, 2 * (size_t)inv_rows_ctas(p)) && !dalloc(A, B, &st->status, 1);
     if (!ok) {
         pd_state_destroy(st);
@@ -660,7 +672,11 @@ static cudaError_t enqueue_dual(pd_plan* p, pd_state* st, const pd_params* prm, 
     if ((e = fwd_fft<R>(p, (const R*)st->xt, (cplx_t<R>*)p->gridb, s))) return e;
     DualArgs da{st->y, st->v, st->block_active, st->eps, st->res_norm};
     if ((e = degrid_dual<R>(p, (const cplx_t<R>*)p->gridb, da, st->act_tiles, st->counts, s))) return e;
-    if ((e = grid_dual<R>(p, da, st->act_tiles, st->counts, st->tile_active, (cplx_t<R>*)st->u, s))) return e;
+    {
+        const int q = p->g.ntiles / 4;
+        const int32_t* lists[4] = {st->act_col, st->act_col + q, st->act_col + 2 * q, st->act_col + 3 * q};
+        if ((e = grid_dual<R>(p, da, lists, st->counts + 2, (cplx_t<R>*)st->u, s))) return e;
+    }
     return cudaSuccess;
 }
 
@@ -696,22 +712,28 @@ static cudaError_t enqueue_iteration(pd_plan* p, pd_state* st, const pd_params* 
 static cudaError_t ensure_per_block(pd_plan* p, pd_state* st) {
     if (st->pb_eye_blocks) return cudaSuccess;
     const int d = p->d, b = p->b, nt = p->g.ntiles;
-    std::vector<int32_t> eyed((size_t)d * d, 0), eyeb((size_t)b * b, 0), flags((size_t)d * nt, 0);
+    std::vector<int32_t> eyed((size_t)d * d, 0), eyeb((size_t)b * b, 0);
     for (int i = 0; i < d; ++i) eyed[(size_t)i * d + i] = 1;
     for (int j = 0; j < b; ++j) eyeb[(size_t)j * b + j] = 1;
-    std::vector<std::vector<int32_t>> tl(d);
+    // each block's tiles, all of them (degridding) and by colour (gridding)
+    std::vector<std::vector<int32_t>> tl(d), tc((size_t)4 * d);
     for (int t = 0; t < nt; ++t)
         for (int sg = p->h_tile_seg_start[t]; sg < p->h_tile_seg_start[t + 1]; ++sg) {
             const int blk = p->h_seg_block[sg];
             tl[blk].push_back(t);
-            flags[(size_t)blk * nt + t] = 1;
+            tc[(size_t)4 * blk + tile_colour(t, p->g.ntx)].push_back(t);
         }
-    std::vector<int32_t> tiles, counts((size_t)2 * d, 0);
-    st->h_pb_off.assign(d + 1, 0);
+    std::vector<int32_t> tiles, counts((size_t)2 * d, 0), col, ccounts((size_t)4 * d, 0);
+    st->h_pb_off.assign((size_t)5 * d + 1, 0);   // [d + 1] all-tile offsets, then [4 d] colour offsets
     for (int i = 0; i < d; ++i) {
         st->h_pb_off[i] = (int32_t)tiles.size();
         tiles.insert(tiles.end(), tl[i].begin(), tl[i].end());
         counts[2 * i + 1] = (int32_t)tl[i].size();
+        for (int c = 0; c < 4; ++c) {
+            st->h_pb_off[d + 1 + 4 * i + c] = (int32_t)col.size();
+            col.insert(col.end(), tc[(size_t)4 * i + c].begin(), tc[(size_t)4 * i + c].end());
+            ccounts[(size_t)4 * i + c] = (int32_t)tc[(size_t)4 * i + c].size();
+        }
     }
     st->h_pb_off[d] = (int32_t)tiles.size();
     cudaError_t e;
@@ -719,10 +741,13 @@ static cudaError_t ensure_per_block(pd_plan* p, pd_state* st) {
     size_t& B = st->device_bytes;
     if ((e = dalloc(A, B, &st->pb_eye_blocks, eyed.size())) || (e = dalloc(A, B, &st->pb_eye_bases, eyeb.size())) ||
         (e = dalloc(A, B, &st->pb_tiles, std::max<size_t>(tiles.size(), 1))) ||
-        (e = dalloc(A, B, &st->pb_counts, counts.size())) || (e = dalloc(A, B, &st->pb_flags, flags.size())))
+        (e = dalloc(A, B, &st->pb_counts, counts.size())) ||
+        (e = dalloc(A, B, &st->pb_col, std::max<size_t>(col.size(), 1))) ||
+        (e = dalloc(A, B, &st->pb_ccounts, ccounts.size())))
         return e;
     if ((e = upload(st->pb_eye_blocks, eyed)) || (e = upload(st->pb_eye_bases, eyeb)) ||
-        (e = upload(st->pb_tiles, tiles)) || (e = upload(st->pb_counts, counts)) || (e = upload(st->pb_flags, flags)))
+        (e = upload(st->pb_tiles, tiles)) || (e = upload(st->pb_counts, counts)) || (e = upload(st->pb_col, col)) ||
+        (e = upload(st->pb_ccounts, ccounts)))
         return e;
     st->h_act.assign(d, 0);
     st->h_actb.assign(b, 0);
@@ -753,9 +778,9 @@ static cudaError_t enqueue_iteration_per_block(pd_plan* p, pd_state* st, const p
     for (int i = 0; i < d; ++i) {
         if (!st->h_act[i]) continue;
         DualArgs da{st->y, st->v, st->pb_eye_blocks + (size_t)i * d, st->eps, st->res_norm};
-        if ((e = grid_dual<R>(p, da, st->pb_tiles + st->h_pb_off[i], st->pb_counts + 2 * i,
-                              st->pb_flags + (size_t)i * p->g.ntiles, (cplx_t<R>*)st->u, s)))
-            return e;
+        const int32_t* lists[4];
+        for (int c = 0; c < 4; ++c) lists[c] = st->pb_col + st->h_pb_off[d + 1 + 4 * i + c];
+        if ((e = grid_dual<R>(p, da, lists, st->pb_ccounts + 4 * i, (cplx_t<R>*)st->u, s))) return e;
     }
     for (int j = 0; j < b; ++j) {
         if (!st->h_actb[j]) continue;

@@ -16,11 +16,10 @@
 // tile plus a halo of J/2 - 1 cells before and J/2 after:
 // * degridding stages that window of F Z x (held as its half grid: the columns
 //   kx <= nx, the others by conjugate symmetry) in shared memory and gathers from it;
-// * gridding accumulates the window in shared memory, adds the interior to U
-//   (nobody else writes it in that launch) and parks the halo ring; a second
-//   launch adds each tile's neighbours' rings to its border. No global atomics.
-//   For J = 8 the tile's 8 x 8 super-cells are processed in four colour phases
-//   whose footprints are disjoint, so warps update the accumulator without atomics.
+// * gridding accumulates the window in shared memory and adds the whole window
+//   (tile and halo) to U. The tiles are gridded in four launches, one per tile colour
+//   (tile row and column parity): the windows of two tiles of one colour are disjoint,
+//   so no two CTAs of a launch touch the same cell of U. No global atomics.
 #include <algorithm>
 
 #include "common.cuh"
@@ -128,7 +127,8 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                                                 const int32_t* __restrict__ tile_seg_start,
                                                 const int32_t* __restrict__ active, const int32_t* __restrict__ list,
                                                 const int32_t* __restrict__ count, double* __restrict__ seg_part,
-                                                int max_segs, Geo g, R two_over_j, R beta, const KbPoly kp) {
+                                                int max_segs, Geo g, R two_over_j, R beta, const KbPoly kp,
+                                                int* __restrict__ next_tile) {
     using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
     // FP32: the window twice, row stride EP (even), the second copy shifted left by one
@@ -140,11 +140,16 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
     double* part = reinterpret_cast<double*>(win + (PAIRS ? 2 : 1) * g.ext * EP);  // [8 warps][max_segs][2]
     int* act_seg = reinterpret_cast<int*>(part + 16 * max_segs);        // [max_segs]
     int* act_pre = act_seg + max_segs;                                   // [max_segs + 1]
-    __shared__ int nact_s;
+    __shared__ int nact_s, tile_s;
     const int E = g.ext, T = g.tile, H = g.halo_lo;
     const int warp = threadIdx.x >> 5;
     const int n = *count;
-    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    for (;;) {
+        // tiles are taken from the heaviest-first list one at a time by whichever CTA is free
+        if (threadIdx.x == 0) tile_s = atomicAdd(next_tile, 1);
+        __syncthreads();
+        const int w = tile_s;
+        if (w >= n) break;
         const int t = list[w];
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
         const int oy = ty * T, ox = tx * T;
@@ -271,15 +276,6 @@ __global__ void k_block_norms(const double* __restrict__ part, const int32_t* __
 }
 
 // ---------------------------------------------------------------- gridding
-__device__ __forceinline__ int ring_index(int ey, int ex, const Geo& g) {
-    const int H = g.halo_lo, A = g.halo_hi, E = g.ext, T = g.tile;
-    if (ey < H) return ey * E + ex;
-    if (ey >= H + T) return (ey - T) * E + ex;
-    const int base = (H + A) * E;
-    if (ex < H) return base + (ey - H) * H + ex;
-    return base + T * H + (ey - H) * A + (ex - H - T);
-}
-
 // value of visibility m to grid: MODE 0 the input (user order); MODE 1 the dual change
 // v_new - v_old with v_new = scale_i r (step 8), writing v_new.
 template <typename R, int MODE>
@@ -293,26 +289,33 @@ __device__ __forceinline__ cplx_t<R> grid_value(int m, const cplx_t<R>* __restri
     return csub(vn, vo);
 }
 
-// Write the tile's accumulator: interior into U (overwrite in MODE 0, add in MODE 1),
-// halo ring into the tile's ring slot.
-template <typename R, int MODE>
-__device__ __forceinline__ void store_tile(const R* acc, int t, int oy, int ox, cplx_t<R>* __restrict__ U,
-                                           cplx_t<R>* __restrict__ ring, const Geo& g) {
+// U += the tile's E x E window (tile and halo, wrapped periodically), the window's value
+// of cell (ey, ex) given by val(ey, ex). The U reads of a batch of cells go out together.
+template <typename R, class V>
+__device__ __forceinline__ void add_window(cplx_t<R>* __restrict__ U, int oy, int ox, const Geo& g, const V& val) {
     using C2 = cplx_t<R>;
-    const int H = g.halo_lo, T = g.tile, E = g.ext, EE = E * E;
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-        const int iy = i / T, ix = i - iy * T;
-        const int k = (iy + H) * E + ix + H;
-        const int64_t off = panel_off(oy + iy, ox + ix, g.Ky);
-        C2 val = mk<C2>(acc[k], acc[k + EE]);
-        if (MODE == 1) val = cadd(U[off], val);
-        U[off] = val;
-    }
-    C2* rg = ring + (int64_t)t * g.ring;
-    for (int i = threadIdx.x; i < EE; i += blockDim.x) {
-        const int ey = i / E, ex = i - ey * E;
-        if (ey >= H && ey < H + T && ex >= H && ex < H + T) continue;
-        rg[ring_index(ey, ex, g)] = mk<C2>(acc[i], acc[i + EE]);
+    const int E = g.ext, H = g.halo_lo;
+    constexpr int EB = 8;
+    for (int i0 = threadIdx.x; i0 < E * E; i0 += EB * (int)blockDim.x) {
+        C2 uo[EB];
+        int64_t off[EB];
+#pragma unroll
+        for (int k = 0; k < EB; ++k) {
+            const int i = i0 + k * (int)blockDim.x;
+            off[k] = -1;
+            if (i < E * E) {
+                const int ey = i / E, ex = i - ey * E;
+                off[k] = panel_off((oy - H + ey) & (g.Ky - 1), (ox - H + ex) & (g.Kx - 1), g.Ky);
+                uo[k] = U[off[k]];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < EB; ++k) {
+            if (off[k] < 0) break;
+            const int i = i0 + k * (int)blockDim.x;
+            const int ey = i / E, ex = i - ey * E;
+            U[off[k]] = cadd(uo[k], val(ey, ex));
+        }
     }
 }
 
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
                                               const int32_t* __restrict__ seg_block,
                                               const int32_t* __restrict__ tile_seg_start,
                                               const int32_t* __restrict__ list, const int32_t* __restrict__ count,
-                                              cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, int max_segs,
+                                              cplx_t<R>* __restrict__ U, int max_segs,
                                               Geo g, R two_over_j, R beta, const KbPoly kp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     R* acc = reinterpret_cast<R*>(smraw);   // [ext*ext] re then [ext*ext] im
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
             }
         }
         __syncthreads();
-        store_tile<R, MODE>(acc, t, oy, ox, U, ring, g);
+        add_window<R>(U, oy, ox, g, [&](int ey, int ex) { return mk<cplx_t<R>>(acc[ey * E + ex], acc[ey * E + ex + EE]); });
         __syncthreads();
     }
 }
@@ -457,8 +460,8 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
     const R* __restrict__ fxs, const R* __restrict__ fys, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_block,
     const int32_t* __restrict__ tile_seg_start, const int32_t* __restrict__ list, const int32_t* __restrict__ count,
-    cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ ring, int max_segs, Geo g, R two_over_j, R beta,
-    const KbPoly kp) {
+    cplx_t<R>* __restrict__ U, int max_segs, Geo g, R two_over_j, R beta, const KbPoly kp,
+    int* __restrict__ next_tile) {
     static_assert(J <= 8 && J % 2 == 0, "class ownership needs J <= 8");
     using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -481,8 +484,14 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
     int* skey = skey_all + warp * 32;
     __shared__ int nact_s;
     const int lcy = lane >> 2, lcx = (lane & 3) * 2;
+    __shared__ int tile_s;
     const int n = *count;
-    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    for (;;) {
+        // tiles are taken from the heaviest-first list one at a time by whichever CTA is free
+        if (threadIdx.x == 0) tile_s = atomicAdd(next_tile, 1);
+        __syncthreads();
+        const int w = tile_s;
+        if (w >= n) break;
         const int t = list[w];
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
         const int oy = ty * T, ox = tx * T;
@@ -503,6 +512,7 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
         // assignment, so the summation order and the result do not vary between runs)
         const int nchunk = (total + 31) >> 5;
         int j = 0;            // this lane's segment cursor (its positions only grow)
+        int mykey = -1;       // super-row of this lane's staged point
         GridIn<R> in{};
         int chunk = warp;
         if (chunk < nchunk && chunk * 32 + lane < total)
@@ -537,7 +547,7 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
                     const int sidx = gam + a;                           // column offset from g
                     *reinterpret_cast<C2*>(cr + 2 * (sidx & 7)) = sidx >= 8 ? mk<C2>(R(0), wv) : mk<C2>(wv, R(0));
                 }
-                skey[lane] = (r0 << 16) | (c0 & ~7);
+                mykey = (r0 << 16) | (c0 & ~7);
             }
             // the next chunk's loads go out now and land while this one is accumulated
             const int nxt = chunk + GW_WARPS;
@@ -545,31 +555,34 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
                 grid_load<R, MODE>(in, nxt * 32 + lane, j, act_pre, act_start, act_scale, src, rbuf, v, cell, fxs,
                                    fys, perm);
             __syncwarp();
-            int cur = -1;
-            C2 lo0 = mk<C2>(R(0), R(0)), hi0 = lo0, lo1 = lo0, hi1 = lo0;
-#pragma unroll 2
-            for (int q = 0; q < fill; ++q) {
-                const int key = skey[q];
-                const C2 ry = rrec[q * GW_RREC + lcy];
+            // runs of consecutive points with the same super-row: one set of running sums
+            // per run, added to the window at its end
+            const int myk = lane < fill ? mykey : -1;
+            const int prevk = __shfl_up_sync(0xffffffffu, myk, 1);
+            unsigned starts = __ballot_sync(0xffffffffu, lane < fill && (lane == 0 || myk != prevk));
+            while (starts) {
+                const int q0 = __ffs(starts) - 1;
+                starts &= starts - 1;
+                const int q1 = starts ? __ffs(starts) - 1 : fill;
+                const int key = __shfl_sync(0xffffffffu, myk, q0);
+                C2 lo0 = mk<C2>(R(0), R(0)), hi0 = lo0, lo1 = lo0, hi1 = lo0;
+                C2 ry = rrec[q0 * GW_RREC + lcy];
                 R wl0, wh0, wl1, wh1;
-                ld4(crec + q * GW_CREC + 2 * lcx, wl0, wh0, wl1, wh1);
-                if (key != cur) {                                       // warp-uniform
-                    if (cur >= 0) {
-                        const int r0 = cur >> 16, g0 = cur & 0xFFFF;
-                        C2* cp = win + (r0 + ((lcy - r0) & 7)) * EP + g0 + lcx;
-                        add2(cp, lo0, lo1);
-                        add2(cp + 8, hi0, hi1);
-                        lo0 = hi0 = lo1 = hi1 = mk<C2>(R(0), R(0));
+                ld4(crec + q0 * GW_CREC + 2 * lcx, wl0, wh0, wl1, wh1);
+                for (int q = q0; q < q1; ++q) {
+                    C2 ryn = ry;
+                    R nl0 = wl0, nh0 = wh0, nl1 = wl1, nh1 = wh1;
+                    if (q + 1 < q1) {
+                        ryn = rrec[(q + 1) * GW_RREC + lcy];
+                        ld4(crec + (q + 1) * GW_CREC + 2 * lcx, nl0, nh0, nl1, nh1);
                     }
-                    cur = key;
+                    lo0.x += wl0 * ry.x; lo0.y += wl0 * ry.y;
+                    hi0.x += wh0 * ry.x; hi0.y += wh0 * ry.y;
+                    lo1.x += wl1 * ry.x; lo1.y += wl1 * ry.y;
+                    hi1.x += wh1 * ry.x; hi1.y += wh1 * ry.y;
+                    ry = ryn; wl0 = nl0; wh0 = nh0; wl1 = nl1; wh1 = nh1;
                 }
-                lo0.x += wl0 * ry.x; lo0.y += wl0 * ry.y;
-                hi0.x += wh0 * ry.x; hi0.y += wh0 * ry.y;
-                lo1.x += wl1 * ry.x; lo1.y += wl1 * ry.y;
-                hi1.x += wh1 * ry.x; hi1.y += wh1 * ry.y;
-            }
-            if (cur >= 0) {
-                const int r0 = cur >> 16, g0 = cur & 0xFFFF;
+                const int r0 = key >> 16, g0 = key & 0xFFFF;
                 C2* cp = win + (r0 + ((lcy - r0) & 7)) * EP + g0 + lcx;
                 add2(cp, lo0, lo1);
                 add2(cp + 8, hi0, hi1);
@@ -577,92 +590,15 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
             __syncwarp();
         }
         __syncthreads();
-        // sum of the warps' windows: interior into U, halo ring into the ring slot; the U
-        // reads of a batch of cells go out together
-        const int H = g.halo_lo;
-        C2* rg = ring + (int64_t)t * g.ring;
-        constexpr int EB = 8;
-        for (int i0 = threadIdx.x; i0 < E * E; i0 += EB * (int)blockDim.x) {
-            C2 uo[EB];
-            int64_t off[EB];
+        // U += the sum of the warps' windows (tile and halo)
+        add_window<R>(U, oy, ox, g, [&](int ey, int ex) {
+            const int kk = ey * EP + ex;
+            C2 sum = wins[kk];
 #pragma unroll
-            for (int k = 0; k < EB; ++k) {
-                const int i = i0 + k * (int)blockDim.x;
-                off[k] = -1;
-                uo[k] = mk<C2>(R(0), R(0));
-                if (i < E * E) {
-                    const int ey = i / E, ex = i - ey * E;
-                    if (ey >= H && ey < H + T && ex >= H && ex < H + T) {
-                        off[k] = panel_off(oy + ey - H, ox + ex - H, g.Ky);
-                        if (MODE == 1) uo[k] = U[off[k]];
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < EB; ++k) {
-                const int i = i0 + k * (int)blockDim.x;
-                if (i >= E * E) break;
-                const int ey = i / E, ex = i - ey * E;
-                const int kk = ey * EP + ex;
-                C2 sum = wins[kk];
-#pragma unroll
-                for (int ww = 1; ww < GW_WARPS; ++ww) sum = cadd(sum, wins[(size_t)ww * WS + kk]);
-                if (off[k] >= 0) U[off[k]] = cadd(uo[k], sum);
-                else rg[ring_index(ey, ex, g)] = sum;
-            }
-        }
+            for (int ww = 1; ww < GW_WARPS; ++ww) sum = cadd(sum, wins[(size_t)ww * WS + kk]);
+            return sum;
+        });
         __syncthreads();
-    }
-}
-
-// Add the neighbours' halo rings to each tile's border cells (periodic grid). Only the
-// cells within A = J/2 of the tile's start or H = J/2 - 1 of its end can receive ring
-// contributions: A*T + H*T cells in full rows plus (A + H) cells in each middle row.
-template <typename R>
-__global__ void __launch_bounds__(256) k_halo_merge(cplx_t<R>* __restrict__ U, const cplx_t<R>* __restrict__ ring,
-                                                    const int32_t* __restrict__ flag, Geo g) {
-    using C2 = cplx_t<R>;
-    const int H = g.halo_lo, A = g.halo_hi, T = g.tile, E = g.ext;
-    const int nborder = (A + H) * T + (T - A - H) * (A + H);
-    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-        const int ty = t / g.ntx, tx = t - ty * g.ntx;
-        int nb[9];
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int dy = k / 3 - 1, dx = k % 3 - 1;
-            const int nty = (ty + dy + g.nty) % g.nty, ntx = (tx + dx + g.ntx) % g.ntx;
-            nb[k] = nty * g.ntx + ntx;
-            if (k != 4 && flag[nb[k]]) any = true;
-        }
-        if (!any) continue;
-        for (int i = threadIdx.x; i < nborder; i += blockDim.x) {
-            int iy, ix;
-            if (i < A * T) { iy = i / T; ix = i - iy * T; }
-            else if (i < (A + H) * T) { const int k = i - A * T; iy = T - H + k / T; ix = k - (k / T) * T; }
-            else {
-                const int k = i - (A + H) * T, w = A + H;
-                iy = A + k / w;
-                const int c = k - (k / w) * w;
-                ix = c < A ? c : T - H + (c - A);
-            }
-            C2 sum = mk<C2>(R(0), R(0));
-            bool hit = false;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                if (k == 4) continue;
-                const int dy = k / 3 - 1, dx = k % 3 - 1;
-                const int ey = iy - dy * T + H, ex = ix - dx * T + H;
-                if (ey < 0 || ey >= E || ex < 0 || ex >= E) continue;
-                if (!flag[nb[k]]) continue;
-                sum = cadd(sum, ring[(int64_t)nb[k] * g.ring + ring_index(ey, ex, g)]);
-                hit = true;
-            }
-            if (hit) {
-                const int64_t off = panel_off(ty * T + iy, tx * T + ix, g.Ky);
-                U[off] = cadd(U[off], sum);
-            }
-        }
     }
 }
 
@@ -695,11 +631,12 @@ static cudaError_t launch_degrid(const pd_plan* p, const cplx_t<R>* grid, cplx_t
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid<R, J, MODE>, 256, smem) == cudaSuccess &&
         per_sm > 0)
         ctas = std::min(ctas, per_sm * p->num_sms);
+    if ((e = cudaMemsetAsync(p->sched + 4, 0, sizeof(int32_t), s))) return e;
     k_degrid<R, J, MODE><<<ctas, 256, smem, s>>>(
         grid, out, a ? (const cplx_t<R>*)a->y : nullptr, a ? (const cplx_t<R>*)a->v : nullptr,
         (cplx_t<R>*)p->rbuf, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start, p->seg_block,
         p->tile_seg_start, a ? a->block_active : nullptr, tiles, count, p->seg_part, ms, g, R(2.0 / g.J),
-        R(g.beta), p->kbpoly);
+        R(g.beta), p->kbpoly, p->sched + 4);
     return cudaGetLastError();
 }
 
@@ -747,7 +684,7 @@ cudaError_t degrid_res_norms(const pd_plan* p, const cplx_t<R>* grid, const cplx
 
 template <typename R, int J, int MODE>
 static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const DualArgs* a, const int32_t* tiles,
-                                 const int32_t* count, cplx_t<R>* U, cudaStream_t s) {
+                                 const int32_t* count, cplx_t<R>* U, int* next_tile, cudaStream_t s) {
     const Geo& g = p->g;
     const int ms = std::max(p->max_tile_segs, 1);
     const size_t lists = (size_t)(2 * ms + 1) * sizeof(int);
@@ -767,48 +704,52 @@ static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const D
             ctas8 = std::min(ctas8, per_sm * p->num_sms);
         k_grid8w<R, J, MODE><<<ctas8, GW_WARPS * 32, smem8, s>>>(
             src, rb, vv, (const R*)p->blk_scale, act, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm,
-            p->seg_start, p->seg_block, p->tile_seg_start, tiles, count, U, (cplx_t<R>*)p->ringbuf, ms, g, toj,
-            beta, p->kbpoly);
+            p->seg_start, p->seg_block, p->tile_seg_start, tiles, count, U, ms, g, toj, beta, p->kbpoly, next_tile);
     } else {
         const size_t smem = (size_t)2 * g.ext * g.ext * sizeof(R) + lists;
         if ((e = ensure_smem(k_grid<R, J, MODE>, smem))) return e;
         k_grid<R, J, MODE><<<ctas, 256, smem, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell,
                                                   (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start,
-                                                  p->seg_block, p->tile_seg_start, tiles, count, U,
-                                                  (cplx_t<R>*)p->ringbuf, ms, g, toj, beta, p->kbpoly);
+                                                  p->seg_block, p->tile_seg_start, tiles, count, U, ms, g, toj,
+                                                  beta, p->kbpoly);
     }
     return cudaGetLastError();
 }
 
+// One launch per tile colour (their windows are disjoint within a colour), each taking
+// its tiles from a dynamically claimed position of its list.
 template <typename R>
 static cudaError_t launch_grid(const pd_plan* p, int mode, const cplx_t<R>* src, const DualArgs* a,
-                               const int32_t* tiles, const int32_t* count, const int32_t* flags, cplx_t<R>* U,
-                               cudaStream_t s) {
+                               const int32_t* const* tiles, const int32_t* counts4, cplx_t<R>* U, cudaStream_t s) {
     const Geo& g = p->g;
     cudaError_t e = cudaSuccess;
     prof_mark(PH_GRID, 0, s);
-    if (mode == 0) {
-        PD_J_DISPATCH(g.J, (e = launch_grid_j<R, JJ, 0>(p, src, a, tiles, count, U, s)));
-    } else {
-        PD_J_DISPATCH(g.J, (e = launch_grid_j<R, JJ, 1>(p, src, a, tiles, count, U, s)));
+    if ((e = cudaMemsetAsync(p->sched, 0, 4 * sizeof(int32_t), s))) return e;
+    for (int c = 0; c < 4 && !e; ++c) {
+        if (mode == 0) {
+            PD_J_DISPATCH(g.J, (e = launch_grid_j<R, JJ, 0>(p, src, a, tiles[c], counts4 + c, U, p->sched + c, s)));
+        } else {
+            PD_J_DISPATCH(g.J, (e = launch_grid_j<R, JJ, 1>(p, src, a, tiles[c], counts4 + c, U, p->sched + c, s)));
+        }
     }
     prof_mark(PH_GRID, 1, s);
-    if (e) return e;
-    prof_mark(PH_HALO, 0, s);
-    k_halo_merge<R><<<std::min(g.ntiles, p->num_sms * 8), 256, 0, s>>>(U, (const cplx_t<R>*)p->ringbuf, flags, g);
-    prof_mark(PH_HALO, 1, s);
-    return cudaGetLastError();
+    return e ? e : cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t grid_plain(const pd_plan* p, const cplx_t<R>* y_user, cplx_t<R>* U, cudaStream_t s) {
-    return launch_grid<R>(p, 0, y_user, nullptr, p->tile_order, p->counts_all + 1, p->tile_ones, U, s);
+    // U = G^T y: every window is added to a zeroed grid
+    cudaError_t e = cudaMemsetAsync(U, 0, (size_t)p->g.Kx * p->g.Ky * sizeof(cplx_t<R>), s);
+    if (e) return e;
+    const int q = p->g.ntiles / 4;
+    const int32_t* lists[4] = {p->colour_tiles, p->colour_tiles + q, p->colour_tiles + 2 * q, p->colour_tiles + 3 * q};
+    return launch_grid<R>(p, 0, y_user, nullptr, lists, p->colour_counts, U, s);
 }
 
 template <typename R>
-cudaError_t grid_dual(const pd_plan* p, const DualArgs& a, const int32_t* tiles, const int32_t* counts,
-                      const int32_t* tile_active, cplx_t<R>* U, cudaStream_t s) {
-    return launch_grid<R>(p, 1, nullptr, &a, tiles, counts + 1, tile_active, U, s);
+cudaError_t grid_dual(const pd_plan* p, const DualArgs& a, const int32_t* const* tiles, const int32_t* counts4,
+                      cplx_t<R>* U, cudaStream_t s) {
+    return launch_grid<R>(p, 1, nullptr, &a, tiles, counts4, U, s);
 }
 
 template cudaError_t degrid_plain<float>(const pd_plan*, const float2*, float2*, cudaStream_t);
@@ -821,9 +762,9 @@ template cudaError_t degrid_dual<double>(const pd_plan*, const double2*, const D
                                          const int32_t*, cudaStream_t);
 template cudaError_t grid_plain<float>(const pd_plan*, const float2*, float2*, cudaStream_t);
 template cudaError_t grid_plain<double>(const pd_plan*, const double2*, double2*, cudaStream_t);
-template cudaError_t grid_dual<float>(const pd_plan*, const DualArgs&, const int32_t*, const int32_t*,
-                                      const int32_t*, float2*, cudaStream_t);
-template cudaError_t grid_dual<double>(const pd_plan*, const DualArgs&, const int32_t*, const int32_t*,
-                                       const int32_t*, double2*, cudaStream_t);
+template cudaError_t grid_dual<float>(const pd_plan*, const DualArgs&, const int32_t* const*, const int32_t*,
+                                      float2*, cudaStream_t);
+template cudaError_t grid_dual<double>(const pd_plan*, const DualArgs&, const int32_t* const*, const int32_t*,
+                                       double2*, cudaStream_t);
 
 }  // namespace pdgb

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(SEL_NT) k_select(
     const double* __restrict__ eps, int d, int b, int32_t* __restrict__ block_active,
     int32_t* __restrict__ basis_active, const int32_t* __restrict__ tile_order,
     const int32_t* __restrict__ tile_seg_start, const int32_t* __restrict__ seg_block, int ntiles,
-    int32_t* __restrict__ tile_active, int32_t* __restrict__ act_tiles, int32_t* __restrict__ counts) {
+    int32_t* __restrict__ tile_active, int32_t* __restrict__ act_tiles, int32_t* __restrict__ act_col, int ntx,
+    int32_t* __restrict__ counts) {
     __shared__ int shi[32];
     __shared__ double shd[32];
     __shared__ double q_sh, cap_sh;
@@ -139,11 +140,27 @@ __global__ void __launch_bounds__(SEL_NT) k_select(
         }
         int excl;
         const int total = block_excl_scan(mine, shi, excl);
+        int mc[4] = {0, 0, 0, 0};
         for (int k = k0; k < k1; ++k)
-            if (tile_active[tile_order[k]]) act_tiles[excl++] = tile_order[k];
+            if (tile_active[tile_order[k]]) {
+                act_tiles[excl++] = tile_order[k];
+                mc[tile_colour(tile_order[k], ntx)]++;
+            }
         int sexcl;
         const int stotal = block_excl_scan(segs, shi, sexcl);
         if (tid == 0) { counts[0] = stotal; counts[1] = total; }
+        // the same tiles split by colour (each colour keeps the heaviest-first order)
+        const int q = ntiles / 4;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int cex;
+            const int ctot = block_excl_scan(mc[c], shi, cex);
+            for (int k = k0; k < k1; ++k) {
+                const int tt = tile_order[k];
+                if (tile_active[tt] && tile_colour(tt, ntx) == c) act_col[c * q + cex++] = tt;
+            }
+            if (tid == 0) counts[2 + c] = ctot;
+        }
     }
 }
 
@@ -152,7 +169,7 @@ cudaError_t select_active(const pd_plan* p, pd_state* st, const SelectArgs& a, c
     k_select<<<1, SEL_NT, 0, s>>>(a.seed, a.adaptive, a.n, a.p_min, a.p_max, st->t, st->p_block, st->p_basis,
                                  st->res_norm, st->eps, p->d, p->b, st->block_active, st->basis_active,
                                  p->tile_order, p->tile_seg_start, p->seg_block, p->g.ntiles,
-                                 st->tile_active, st->act_tiles, st->counts);
+                                 st->tile_active, st->act_tiles, st->act_col, p->g.ntx, st->counts);
     prof_mark(PH_SELECT, 1, s);
     return cudaGetLastError();
 }

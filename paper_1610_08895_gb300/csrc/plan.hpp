@@ -26,8 +26,13 @@ struct Geo {
     int ext;        // T + J - 1: extended tile edge of the gridding accumulator
     int halo_lo;    // J/2 - 1 cells before the tile
     int halo_hi;    // J/2 cells after the tile
-    int ring;       // ring cells per tile
 };
+
+// Tile colour classes of the gridding: (tile row parity, tile column parity). Two tiles
+// of one colour are at least two tiles apart, so for J - 1 <= T their windows (tile plus
+// halo) are disjoint and one launch may update them in U without atomics. The grid has
+// at least two tiles per side (an even number), so the four classes are equal in size.
+__host__ __device__ __forceinline__ int tile_colour(int t, int ntx) { return (((t / ntx) & 1) << 1) | ((t % ntx) & 1); }
 
 // Monomial coefficients (in x = 2 f - 1) of the per-tap Chebyshev interpolants of the
 // Kaiser-Bessel weight phi(f + J/2 - 1 - a), used by the FP32 kernels.
@@ -77,6 +82,8 @@ struct pd_plan {
     int32_t* block_seg_start = nullptr;    // [d + 1] into block_seg_list
     int32_t* block_seg_list = nullptr;     // [nseg] segments of each block, tile order
     int32_t* tile_order = nullptr;         // [ntiles] tiles by decreasing visibility count
+    int32_t* colour_tiles = nullptr;       // [4][ntiles/4] tiles of each colour, heaviest first
+    int32_t* colour_counts = nullptr;      // [4] ntiles/4 each
     int32_t* counts_all = nullptr;         // {nseg, ntiles}
     int32_t* ones_block = nullptr;         // all blocks active
     int32_t* ones_basis = nullptr;
@@ -99,11 +106,12 @@ struct pd_plan {
     double* seg_part = nullptr;    // [2 * nseg] per-segment FP64 partial norms
     double* blk_norm = nullptr;    // [2 * d]: ||r_i||^2, ||G_i b - y_i||^2
     void* blk_scale = nullptr;     // real [d]: max(0, 1 - eps_i / ||r_i||)
-    void* ringbuf = nullptr;       // complex [ntiles][ring]
-    int32_t* tile_ones = nullptr;  // [ntiles] all ones (every tile active in plain gridding)
     void* ll[2] = {nullptr, nullptr};  // real [b][ny/2][nx/2] wavelet approximation ping-pong
     void* ds = nullptr;            // real [b][ny][nx] change of the sparsity duals
+    void* synpart = nullptr;       // real [b][ny][nx] level-0 synthesis of each basis
     double* red = nullptr;         // reduction scratch
+    int32_t* sched = nullptr;      // [8] work counters of the dynamically scheduled launches (0-3 gridding
+                                   // colours, 4 degridding)
     int red_len = 0;
     size_t device_bytes = 0;
     std::vector<void*> allocs;     // every device allocation of the plan
@@ -124,9 +132,10 @@ struct pd_state {
     double* p_basis = nullptr;     // [b]
     int32_t* block_active = nullptr;   // [d]
     int32_t* basis_active = nullptr;   // [b]
-    int32_t* act_tiles = nullptr;      // [ntiles]
+    int32_t* act_tiles = nullptr;      // [ntiles] tiles holding an active block, heaviest first
+    int32_t* act_col = nullptr;        // [4][ntiles/4] the same tiles split by colour
     int32_t* tile_active = nullptr;    // [ntiles]: tile holds a visibility of an active block
-    int32_t* counts = nullptr;         // {active segments, active tiles}
+    int32_t* counts = nullptr;         // {active segments, active tiles, active tiles of colour 0..3}
     int64_t* t = nullptr;              // iteration counter (device)
     double* diag = nullptr;            // [2]: ||dx||^2, ||x||^2
     double* prim_part = nullptr;       // [2 * ny / rows-per-CTA]
@@ -147,7 +156,8 @@ struct pd_state {
     int32_t* pb_eye_bases = nullptr;   // [b][b]
     int32_t* pb_tiles = nullptr;       // tiles of block i at pb_tiles[h_pb_off[i] ...]
     int32_t* pb_counts = nullptr;      // [d][2]: {0, number of tiles of block i}
-    int32_t* pb_flags = nullptr;       // [d][ntiles]: tile holds block i
+    int32_t* pb_col = nullptr;         // tiles of block i and colour c at pb_col[h_pb_off[4 i + c] ...]
+    int32_t* pb_ccounts = nullptr;     // [d][4] number of tiles of block i per colour
     std::vector<int32_t> h_pb_off;
     std::vector<int32_t> h_act, h_actb;
     int64_t h_t = 0;
@@ -207,10 +217,11 @@ cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs&
 // plain grid: U = G^T y_user (U overwritten)
 template <typename R>
 cudaError_t grid_plain(const pd_plan* p, const cplx_t<R>* y_user, cplx_t<R>* U, cudaStream_t s);
-// pd grid over the listed tiles: v <- scale * r, U += G^T (v_new - v_old)
+// pd grid over the listed tiles, one launch per colour (tiles[c]: device list of colour c,
+// counts4[c]: device count): v <- scale * r, U += G^T (v_new - v_old)
 template <typename R>
-cudaError_t grid_dual(const pd_plan* p, const DualArgs& a, const int32_t* tiles, const int32_t* counts,
-                      const int32_t* tile_active, cplx_t<R>* U, cudaStream_t s);
+cudaError_t grid_dual(const pd_plan* p, const DualArgs& a, const int32_t* const* tiles, const int32_t* counts4,
+                      cplx_t<R>* U, cudaStream_t s);
 
 // ---- wavelet.cu
 // plain analysis: coeffs[b][ny][nx] = Psi^H x

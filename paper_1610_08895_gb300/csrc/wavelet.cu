@@ -29,6 +29,129 @@ constexpr int NT_W = 256;
 template <typename R> __device__ __forceinline__ R clip(R v, R a) { return v > a ? a : (v < -a ? -a : v); }
 
 // -------------------------------------------------------------------- analysis
+// The filter pair of one basis in registers: h (low-pass) and g_j = (-1)^j h_{LF-1-j}.
+template <typename R, int LF>
+__device__ __forceinline__ void load_filters(const R* __restrict__ filt, int k, R* h, R* g) {
+#pragma unroll
+    for (int j = 0; j < LF; ++j) {
+        h[j] = filt[k * MAX_FILTER + j];
+        g[j] = ((j & 1) ? R(-1) : R(1)) * filt[k * MAX_FILTER + LF - 1 - j];
+    }
+}
+
+// Dispatch on the filter length of basis k (2, 4, ..., 16: db1 .. db8) to a body with the
+// length as a compile-time constant (fully unrolled taps, filters in registers).
+#define PD_LF_DISPATCH(lf_, CALL)                           \
+    switch (lf_) {                                          \
+        case 2: { constexpr int LF = 2; CALL; } break;      \
+        case 4: { constexpr int LF = 4; CALL; } break;      \
+        case 6: { constexpr int LF = 6; CALL; } break;      \
+        case 8: { constexpr int LF = 8; CALL; } break;      \
+        case 10: { constexpr int LF = 10; CALL; } break;    \
+        case 12: { constexpr int LF = 12; CALL; } break;    \
+        case 14: { constexpr int LF = 14; CALL; } break;    \
+        default: { constexpr int LF = 16; CALL; } break;    \
+    }
+
+constexpr int ARB = 4;   // analysis outputs per thread along a row (row pass) or column (column pass)
+
+// One analysis level of basis k on an output tile of ty x tx per sub-band at (oy0, ox0)
+// of the (my x mx) region. Staged input rows have pitch IWP (a multiple of 4). Row pass:
+// a thread computes ARB consecutive outputs of one input row from LF + 2 ARB - 2 staged
+// values; column pass: ARB consecutive output rows of one column. MODE 0 writes the
+// scaled coefficients, MODE 1 the step-13 update of s and its change ds.
+template <typename R, int MODE, int LF>
+__device__ __forceinline__ void dwt_body(const R* __restrict__ src, R* __restrict__ ll_out, R* __restrict__ out,
+                                         R* __restrict__ ds, const R* __restrict__ filt, int k, int my, int mx,
+                                         int oy0, int ox0, int ty, int tx, bool last, int64_t boff, int nx,
+                                         int64_t ll_off, R scale, R alpha, R* sm) {
+    constexpr int NX = LF + 2 * ARB - 2;               // staged values per ARB outputs
+    const int hy = my >> 1, hx = mx >> 1;
+    const int IH = 2 * ty + LF - 2, IW = 2 * tx + LF - 2, IWP = (IW + 3) & ~3;
+    R* in = sm;                                        // [IH][IWP]
+    R* ra = in + IH * IWP;                             // [IH][tx]
+    R* rd = ra + IH * tx;                              // [IH][tx]
+    R h[LF], g[LF];
+    load_filters<R, LF>(filt, k, h, g);
+    // column-pass work item of this thread: rows r0 .. r0 + ARB - 1 of column c
+    const int ncg = (ty + ARB - 1) / ARB;
+    const int item = threadIdx.x;
+    const bool colwork = item < ncg * tx;
+    const int c = colwork ? item % tx : 0, r0 = colwork ? (item / tx) * ARB : 0;
+    // step 13 reads the current s of this thread's outputs: issue those loads first
+    R s_old[ARB][4];
+    if (MODE == 1 && colwork) {
+#pragma unroll
+        for (int i = 0; i < ARB; ++i) {
+            if (r0 + i < ty) {
+                const int oy = oy0 + r0 + i, ox = ox0 + c;
+                s_old[i][0] = out[boff + (int64_t)oy * nx + hx + ox];
+                s_old[i][1] = out[boff + (int64_t)(hy + oy) * nx + ox];
+                s_old[i][2] = out[boff + (int64_t)(hy + oy) * nx + hx + ox];
+                s_old[i][3] = last ? out[boff + (int64_t)oy * nx + ox] : R(0);
+            }
+        }
+    }
+    stage_batched<8>(in, IH * IWP, [&](int i) {
+        const int r = i / IWP, cc = i - r * IWP;
+        const int gy = (2 * oy0 + r) & (my - 1), gx = (2 * ox0 + cc) & (mx - 1);
+        return src[(int64_t)gy * mx + gx];
+    });
+    __syncthreads();
+    // row pass
+    const int nrg = (tx + ARB - 1) / ARB;
+    for (int it = threadIdx.x; it < IH * nrg; it += blockDim.x) {
+        const int r = it / nrg, c0 = (it - r * nrg) * ARB;
+        const R* row = in + r * IWP + 2 * c0;
+        R x[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) x[i] = (2 * c0 + i < IWP) ? row[i] : R(0);
+#pragma unroll
+        for (int o = 0; o < ARB; ++o) {
+            R a = 0, d = 0;
+#pragma unroll
+            for (int j = 0; j < LF; ++j) { a += h[j] * x[2 * o + j]; d += g[j] * x[2 * o + j]; }
+            if (c0 + o < tx) { ra[r * tx + c0 + o] = a; rd[r * tx + c0 + o] = d; }
+        }
+    }
+    __syncthreads();
+    if (!colwork) return;
+    R va[NX], vd[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+        const int rr = 2 * r0 + i;
+        va[i] = rr < IH ? ra[rr * tx + c] : R(0);
+        vd[i] = rr < IH ? rd[rr * tx + c] : R(0);
+    }
+#pragma unroll
+    for (int o = 0; o < ARB; ++o) {
+        if (r0 + o >= ty) break;
+        R ll = 0, hl = 0, lh = 0, hh = 0;
+#pragma unroll
+        for (int j = 0; j < LF; ++j) {
+            const R a = va[2 * o + j], d = vd[2 * o + j];
+            ll += h[j] * a; lh += g[j] * a;
+            hl += h[j] * d; hh += g[j] * d;
+        }
+        const int oy = oy0 + r0 + o, ox = ox0 + c;
+        const int64_t p_hl = boff + (int64_t)oy * nx + hx + ox;
+        const int64_t p_lh = boff + (int64_t)(hy + oy) * nx + ox;
+        const int64_t p_hh = boff + (int64_t)(hy + oy) * nx + hx + ox;
+        const int64_t p_ll = boff + (int64_t)oy * nx + ox;
+        if (MODE == 0) {
+            out[p_hl] = hl * scale; out[p_lh] = lh * scale; out[p_hh] = hh * scale;
+            if (last) out[p_ll] = ll * scale;
+        } else {
+            R so, sn;
+            so = s_old[o][0]; sn = clip(so + hl * scale, alpha); out[p_hl] = sn; ds[p_hl] = sn - so;
+            so = s_old[o][1]; sn = clip(so + lh * scale, alpha); out[p_lh] = sn; ds[p_lh] = sn - so;
+            so = s_old[o][2]; sn = clip(so + hh * scale, alpha); out[p_hh] = sn; ds[p_hh] = sn - so;
+            if (last) { so = s_old[o][3]; sn = clip(so + ll * scale, alpha); out[p_ll] = sn; ds[p_ll] = sn - so; }
+        }
+        if (!last) ll_out[ll_off + (int64_t)oy * hx + ox] = ll;
+    }
+}
+
 // One level for every basis in blockIdx.z. MODE 0: out = coefficient * scale.
 // MODE 1: s/ds update of step 13. The last level also treats the approximation band.
 template <typename R, int MODE>
@@ -47,78 +170,12 @@ __global__ void __launch_bounds__(NT_W) k_dwt_level(const R* __restrict__ x0, co
     const int ty = min(AT, hy), tx = min(AT, hx);
     const int oy0 = blockIdx.y * ty, ox0 = blockIdx.x * tx;
     if (oy0 >= hy || ox0 >= hx) return;
-    const int IH = 2 * ty + lf - 2, IW = 2 * tx + lf - 2;
-    R* in = reinterpret_cast<R*>(smraw);              // [IH][IW]
-    R* ra = in + IH * IW;                              // [IH][tx]
-    R* rd = ra + IH * tx;                              // [IH][tx]
-    __shared__ R h[MAX_FILTER], g[MAX_FILTER];
-    if (threadIdx.x < lf) {
-        h[threadIdx.x] = filt[k * MAX_FILTER + threadIdx.x];
-        const int j = threadIdx.x;
-        g[j] = ((j & 1) ? R(-1) : R(1)) * filt[k * MAX_FILTER + lf - 1 - j];
-    }
     const R* src = level == 0 ? x0 : ll_in + (int64_t)k * (ny / 2) * (nx / 2);
-    const int64_t boff = (int64_t)k * ny * nx;
+    const int64_t boff = (int64_t)k * ny * nx, ll_off = (int64_t)k * (ny / 2) * (nx / 2);
     const bool last = level == L - 1;
-    // step 13 reads the current s of this thread's outputs: issue those loads first
-    constexpr int PER = AT * AT / NT_W;
-    R s_old[PER][4];
-    if (MODE == 1) {
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int i = threadIdx.x + q * NT_W;
-            if (i < ty * tx) {
-                const int oy = oy0 + i / tx, ox = ox0 + i % tx;
-                s_old[q][0] = out[boff + (int64_t)oy * nx + hx + ox];
-                s_old[q][1] = out[boff + (int64_t)(hy + oy) * nx + ox];
-                s_old[q][2] = out[boff + (int64_t)(hy + oy) * nx + hx + ox];
-                s_old[q][3] = last ? out[boff + (int64_t)oy * nx + ox] : R(0);
-            }
-        }
-    }
-    stage_batched<8>(in, IH * IW, [&](int i) {
-        const int r = i / IW, c = i - r * IW;
-        const int gy = (2 * oy0 + r) & (my - 1), gx = (2 * ox0 + c) & (mx - 1);
-        return src[(int64_t)gy * mx + gx];
-    });
-    __syncthreads();
-    for (int i = threadIdx.x; i < IH * tx; i += blockDim.x) {
-        const int r = i / tx, c = i - r * tx;
-        const R* row = in + r * IW + 2 * c;
-        R a = 0, d = 0;
-        for (int j = 0; j < lf; ++j) { a += h[j] * row[j]; d += g[j] * row[j]; }
-        ra[i] = a;
-        rd[i] = d;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int i = threadIdx.x + q * NT_W;
-        if (i >= ty * tx) break;
-        const int r = i / tx, c = i - r * tx;
-        R ll = 0, hl = 0, lh = 0, hh = 0;
-        for (int j = 0; j < lf; ++j) {
-            const R va = ra[(2 * r + j) * tx + c], vd = rd[(2 * r + j) * tx + c];
-            ll += h[j] * va; lh += g[j] * va;
-            hl += h[j] * vd; hh += g[j] * vd;
-        }
-        const int oy = oy0 + r, ox = ox0 + c;
-        const int64_t p_hl = boff + (int64_t)oy * nx + hx + ox;
-        const int64_t p_lh = boff + (int64_t)(hy + oy) * nx + ox;
-        const int64_t p_hh = boff + (int64_t)(hy + oy) * nx + hx + ox;
-        const int64_t p_ll = boff + (int64_t)oy * nx + ox;
-        if (MODE == 0) {
-            out[p_hl] = hl * scale; out[p_lh] = lh * scale; out[p_hh] = hh * scale;
-            if (last) out[p_ll] = ll * scale;
-        } else {
-            R so, sn;
-            so = s_old[q][0]; sn = clip(so + hl * scale, alpha); out[p_hl] = sn; ds[p_hl] = sn - so;
-            so = s_old[q][1]; sn = clip(so + lh * scale, alpha); out[p_lh] = sn; ds[p_lh] = sn - so;
-            so = s_old[q][2]; sn = clip(so + hh * scale, alpha); out[p_hh] = sn; ds[p_hh] = sn - so;
-            if (last) { so = s_old[q][3]; sn = clip(so + ll * scale, alpha); out[p_ll] = sn; ds[p_ll] = sn - so; }
-        }
-        if (!last) ll_out[(int64_t)k * (ny / 2) * (nx / 2) + (int64_t)oy * hx + ox] = ll;
-    }
+    R* sm = reinterpret_cast<R*>(smraw);
+    PD_LF_DISPATCH(lf, (dwt_body<R, MODE, LF>(src, ll_out, out, ds, filt, k, my, mx, oy0, ox0, ty, tx, last, boff,
+                                              nx, ll_off, scale, alpha, sm)));
 }
 
 // Dirac basis (identity): MODE 0 copies x * scale, MODE 1 applies step 13 elementwise.
@@ -143,22 +200,31 @@ __global__ void k_dirac(const R* __restrict__ x, R* __restrict__ out, R* __restr
 }
 
 // -------------------------------------------------------------------- synthesis
-// Reconstruct an (ty x tx) tile of the level-`level` region (size my x mx) of basis k
-// from its four sub-bands; the approximation band comes from ll_in (or from the
-// packed coefficients at the coarsest level). Result left in `res` (shared).
-template <typename R>
-__device__ void synth_tile(const R* __restrict__ coef, const R* __restrict__ ll_in, int k, int level, int L, int ny,
-                           int nx, int oy0, int ox0, int ty, int tx, const R* h, const R* g, int lf, R* sm, R* res) {
+constexpr int SRP = 2;   // synthesis: output row pairs per thread (column pass), column pairs (row pass)
+
+// Reconstruct a (ty x tx) tile of the level-`level` region (size my x mx) of basis k from
+// its four sub-bands; the approximation band comes from ll_in (or from the packed
+// coefficients at the coarsest level). Result left in `res` (shared, [ty][tx]).
+// Output rows 2m and 2m + 1 both read the sub-band rows m + off - i, i < LF/2 (even and
+// odd taps): a thread computes SRP row pairs of one column from LF/2 + SRP - 1 staged
+// values per band; the row pass likewise along the rows.
+template <typename R, int LF>
+__device__ __forceinline__ void synth_tile(const R* __restrict__ coef, const R* __restrict__ ll_in,
+                                           const R* __restrict__ filt, int k, int level, int L, int ny, int nx,
+                                           int oy0, int ox0, int ty, int tx, R* sm, R* res) {
+    constexpr int NV = LF / 2 + SRP - 1, OFF = LF / 2 - 1;
     const int my = ny >> level, mx = nx >> level;
     const int hy = my >> 1, hx = mx >> 1;
-    const int NKy = ty / 2 + lf / 2 - 1, NKx = tx / 2 + lf / 2 - 1;
-    const int kby = oy0 / 2 - lf / 2 + 1, kbx = ox0 / 2 - lf / 2 + 1;
+    const int NKy = ty / 2 + LF / 2 - 1, NKx = tx / 2 + LF / 2 - 1;
+    const int kby = oy0 / 2 - LF / 2 + 1, kbx = ox0 / 2 - LF / 2 + 1;
     R* LLs = sm;                      // [NKy][NKx] x4 sub-bands
     R* HLs = LLs + NKy * NKx;
     R* LHs = HLs + NKy * NKx;
     R* HHs = LHs + NKy * NKx;
     R* lo = HHs + NKy * NKx;          // [ty][NKx] columns synthesised, low-x half
     R* hi = lo + ty * NKx;
+    R h[LF], g[LF];
+    load_filters<R, LF>(filt, k, h, g);
     const int64_t boff = (int64_t)k * ny * nx;
     const bool coarsest = level == L - 1;
     const R* llsrc = ll_in + (int64_t)k * (ny / 2) * (nx / 2);
@@ -184,41 +250,80 @@ __device__ void synth_tile(const R* __restrict__ coef, const R* __restrict__ ll_
         }
     }
     __syncthreads();
-    const int off = lf / 2 - 1;
-    for (int i = threadIdx.x; i < ty * NKx; i += blockDim.x) {
-        const int r = i / NKx, c = i - r * NKx;
-        R l = 0, hh = 0;
-        for (int j = r & 1; j < lf; j += 2) {
-            const int kk = ((r - j) >> 1) + off;
-            l += h[j] * LLs[kk * NKx + c] + g[j] * LHs[kk * NKx + c];
-            hh += h[j] * HLs[kk * NKx + c] + g[j] * HHs[kk * NKx + c];
+    // column pass: rows 2m .. 2m + 2 SRP - 1 of column c of lo and hi
+    const int npr = (ty / 2 + SRP - 1) / SRP;
+    for (int it = threadIdx.x; it < npr * NKx; it += blockDim.x) {
+        const int c = it % NKx, m0 = (it / NKx) * SRP;
+        R a[4][NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int kk = m0 + OFF - (LF / 2 - 1) + i;      // sub-band rows m0 + OFF - (LF/2 - 1) ...
+            const bool ok = kk < NKy;
+            a[0][i] = ok ? LLs[kk * NKx + c] : R(0);
+            a[1][i] = ok ? LHs[kk * NKx + c] : R(0);
+            a[2][i] = ok ? HLs[kk * NKx + c] : R(0);
+            a[3][i] = ok ? HHs[kk * NKx + c] : R(0);
         }
-        lo[i] = l;
-        hi[i] = hh;
+#pragma unroll
+        for (int pq = 0; pq < SRP; ++pq) {
+            const int m = m0 + pq;
+            if (2 * m >= ty) break;
+#pragma unroll
+            for (int par = 0; par < 2; ++par) {
+                R l = 0, hh = 0;
+#pragma unroll
+                for (int i = 0; i < LF / 2; ++i) {
+                    // tap j = 2 i + par reads sub-band row m + OFF - i = a[.][pq + LF/2 - 1 - i]
+                    const int j = 2 * i + par, q = pq + LF / 2 - 1 - i;
+                    l += h[j] * a[0][q] + g[j] * a[1][q];
+                    hh += h[j] * a[2][q] + g[j] * a[3][q];
+                }
+                lo[(2 * m + par) * NKx + c] = l;
+                hi[(2 * m + par) * NKx + c] = hh;
+            }
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < ty * tx; i += blockDim.x) {
-        const int r = i / tx, c = i - r * tx;
-        R v = 0;
-        for (int j = c & 1; j < lf; j += 2) {
-            const int kk = ((c - j) >> 1) + off;
-            v += h[j] * lo[r * NKx + kk] + g[j] * hi[r * NKx + kk];
+    // row pass: columns 2m .. 2m + 2 SRP - 1 of row r
+    const int npc = (tx / 2 + SRP - 1) / SRP;
+    for (int it = threadIdx.x; it < ty * npc; it += blockDim.x) {
+        const int r = it / npc, m0 = (it - r * npc) * SRP;
+        R bl[NV], bh[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int kk = m0 + i;
+            bl[i] = kk < NKx ? lo[r * NKx + kk] : R(0);
+            bh[i] = kk < NKx ? hi[r * NKx + kk] : R(0);
         }
-        res[i] = v;
+#pragma unroll
+        for (int pq = 0; pq < SRP; ++pq) {
+            const int m = m0 + pq;
+            if (2 * m >= tx) break;
+#pragma unroll
+            for (int par = 0; par < 2; ++par) {
+                R v = 0;
+#pragma unroll
+                for (int i = 0; i < LF / 2; ++i) {
+                    const int j = 2 * i + par, q = pq + LF / 2 - 1 - i;
+                    v += h[j] * bl[q] + g[j] * bh[q];
+                }
+                res[r * tx + 2 * m + par] = v;
+            }
+        }
     }
     __syncthreads();
 }
 
-// Levels L-1 .. 1 of one basis per blockIdx.z: reconstruct the (ny>>level) x (nx>>level)
-// approximation of the next finer level into ll_out.
+// One level of one basis per blockIdx.z: reconstruct the (ny>>level) x (nx>>level)
+// approximation of the next finer level into ll_out + basis * out_stride (at level 0:
+// the basis's full-size synthesis).
 template <typename R>
 __global__ void __launch_bounds__(NT_W) k_idwt_level(const R* __restrict__ coef, const R* __restrict__ ll_in,
                                                      R* __restrict__ ll_out, const R* __restrict__ filt,
                                                      const int32_t* __restrict__ flen,
                                                      const int32_t* __restrict__ active, int level, int L, int ny,
-                                                     int nx) {
+                                                     int nx, int64_t out_stride) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ R h[MAX_FILTER], g[MAX_FILTER];
     const int k = blockIdx.z;
     const int lf = flen[k];
     if (lf == 0) return;
@@ -227,84 +332,63 @@ __global__ void __launch_bounds__(NT_W) k_idwt_level(const R* __restrict__ coef,
     const int ty = min(ST, my), tx = min(ST, mx);
     const int oy0 = blockIdx.y * ty, ox0 = blockIdx.x * tx;
     if (oy0 >= my || ox0 >= mx) return;
-    if (threadIdx.x < lf) {
-        const int j = threadIdx.x;
-        h[j] = filt[k * MAX_FILTER + j];
-        g[j] = ((j & 1) ? R(-1) : R(1)) * filt[k * MAX_FILTER + lf - 1 - j];
-    }
-    __syncthreads();
     R* sm = reinterpret_cast<R*>(smraw);
     R* res = sm + 4 * (ty / 2 + MAX_FILTER / 2) * (tx / 2 + MAX_FILTER / 2) + 2 * ty * (tx / 2 + MAX_FILTER / 2);
-    synth_tile<R>(coef, ll_in, k, level, L, ny, nx, oy0, ox0, ty, tx, h, g, lf, sm, res);
-    R* dst = ll_out + (int64_t)k * (ny / 2) * (nx / 2);
+    PD_LF_DISPATCH(lf, (synth_tile<R, LF>(coef, ll_in, filt, k, level, L, ny, nx, oy0, ox0, ty, tx, sm, res)));
+    R* dst = ll_out + (int64_t)k * out_stride;
     for (int i = threadIdx.x; i < ty * tx; i += blockDim.x) {
         const int r = i / tx, c = i - r * tx;
         dst[(int64_t)(oy0 + r) * mx + ox0 + c] = res[i];
     }
 }
 
-// Level 0 for all bases at once: acc = sum_k Psi_k coef_k over active bases (Dirac
-// included); MODE 0: out = acc * scale, MODE 1: out += acc * scale (s~ update).
-template <typename R, int MODE>
-__global__ void __launch_bounds__(NT_W) k_idwt_final(const R* __restrict__ coef, const R* __restrict__ ll_in,
-                                                     R* __restrict__ out, const R* __restrict__ filt,
-                                                     const int32_t* __restrict__ flen,
-                                                     const int32_t* __restrict__ active, int b, int L, int ny,
-                                                     int nx, R scale) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ R h[MAX_FILTER], g[MAX_FILTER];
-    constexpr int PER = ST * ST / NT_W;
-    const int ty = min(ST, ny), tx = min(ST, nx);
-    const int oy0 = blockIdx.y * ty, ox0 = blockIdx.x * tx;
-    R acc[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) acc[q] = 0;
-    R* sm = reinterpret_cast<R*>(smraw);
-    R* res = sm + 4 * (ty / 2 + MAX_FILTER / 2) * (tx / 2 + MAX_FILTER / 2) + 2 * ty * (tx / 2 + MAX_FILTER / 2);
-    for (int k = 0; k < b; ++k) {
-        if (MODE == 1 && !active[k]) continue;
-        const int lf = flen[k];
-        if (lf == 0) {
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int i = threadIdx.x + q * NT_W;
-                if (i < ty * tx) {
-                    const int r = i / tx, c = i - r * tx;
-                    acc[q] += coef[(int64_t)k * ny * nx + (int64_t)(oy0 + r) * nx + ox0 + c];
-                }
-            }
-            continue;
-        }
-        __syncthreads();
-        if (threadIdx.x < lf) {
-            const int j = threadIdx.x;
-            h[j] = filt[k * MAX_FILTER + j];
-            g[j] = ((j & 1) ? R(-1) : R(1)) * filt[k * MAX_FILTER + lf - 1 - j];
-        }
-        __syncthreads();
-        synth_tile<R>(coef, ll_in, k, 0, L, ny, nx, oy0, ox0, ty, tx, h, g, lf, sm, res);
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int i = threadIdx.x + q * NT_W;
-            if (i < ty * tx) acc[q] += res[i];
-        }
+// Sum of the bases' level-0 syntheses (the Dirac basis is its coefficients) over the
+// active bases in basis order: MODE 0: out = acc * scale, MODE 1: out += acc * scale
+// (the s~ update of step 14). Four consecutive pixels per thread.
+template <typename R> struct Quad { R a, b, c, d; };
+template <typename R> __device__ __forceinline__ Quad<R> ldq(const R* p) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        return {q.x, q.y, q.z, q.w};
+    } else {
+        const double2 q0 = *reinterpret_cast<const double2*>(p), q1 = *reinterpret_cast<const double2*>(p + 2);
+        return {q0.x, q0.y, q1.x, q1.y};
     }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int i = threadIdx.x + q * NT_W;
-        if (i < ty * tx) {
-            const int r = i / tx, c = i - r * tx;
-            const int64_t o = (int64_t)(oy0 + r) * nx + ox0 + c;
-            if (MODE == 0) out[o] = acc[q] * scale;
-            else out[o] += acc[q] * scale;
+}
+template <typename R> __device__ __forceinline__ void stq(R* p, const Quad<R>& v) {
+    if constexpr (sizeof(R) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v.a, v.b, v.c, v.d);
+    } else {
+        *reinterpret_cast<double2*>(p) = make_double2(v.a, v.b);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(v.c, v.d);
+    }
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) k_syn_sum(const R* __restrict__ coef, const R* __restrict__ part,
+                                                 const int32_t* __restrict__ flen, const int32_t* __restrict__ active,
+                                                 int b, int64_t n, R* __restrict__ out, R scale) {
+    for (int64_t i4 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; 4 * i4 < n; i4 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = 4 * i4;
+        Quad<R> acc{R(0), R(0), R(0), R(0)};
+        for (int k = 0; k < b; ++k) {
+            if (MODE == 1 && !active[k]) continue;
+            const Quad<R> v = ldq((flen[k] == 0 ? coef : part) + (int64_t)k * n + i);
+            acc.a += v.a; acc.b += v.b; acc.c += v.c; acc.d += v.d;
         }
+        Quad<R> o{acc.a * scale, acc.b * scale, acc.c * scale, acc.d * scale};
+        if (MODE == 1) {
+            const Quad<R> prev = ldq(out + i);
+            o.a += prev.a; o.b += prev.b; o.c += prev.c; o.d += prev.d;
+        }
+        stq(out + i, o);
     }
 }
 
 // -------------------------------------------------------------------- launchers
 template <typename R> static size_t ana_smem(int ty, int tx) {
-    const int IH = 2 * ty + MAX_FILTER - 2, IW = 2 * tx + MAX_FILTER - 2;
-    return (size_t)(IH * IW + 2 * IH * tx) * sizeof(R);
+    const int IH = 2 * ty + MAX_FILTER - 2, IWP = (2 * tx + MAX_FILTER - 2 + 3) & ~3;
+    return (size_t)(IH * IWP + 2 * IH * tx) * sizeof(R);
 }
 template <typename R> static size_t syn_smem(int ty, int tx) {
     const int NKy = ty / 2 + MAX_FILTER / 2, NKx = tx / 2 + MAX_FILTER / 2;
@@ -350,29 +434,27 @@ static cudaError_t synthesis(const pd_plan* p, const R* coef, R* out, const int3
     cudaError_t e;
     const int ny = p->g.ny, nx = p->g.nx, b = p->b, L = p->L;
     const R scale = R(1.0 / std::sqrt((double)b));
+    const int64_t n = (int64_t)ny * nx;
     if (p->n_wavelet > 0) {
-        for (int lev = L - 1; lev >= 1; --lev) {
+        for (int lev = L - 1; lev >= 0; --lev) {
             const int my = ny >> lev, mx = nx >> lev;
             const int ty = std::min(ST, my), tx = std::min(ST, mx);
             dim3 grid((mx + tx - 1) / tx, (my + ty - 1) / ty, b);
             if ((e = ensure_smem(k_idwt_level<R>, syn_smem<R>(ty, tx)))) return e;
+            // levels L-1 .. 1 rebuild the approximations, level 0 each basis's full image
+            R* dst = lev > 0 ? (R*)p->ll[lev & 1] : (R*)p->synpart;
+            const int64_t stride = lev > 0 ? (int64_t)(ny / 2) * (nx / 2) : n;
             k_idwt_level<R><<<grid, NT_W, syn_smem<R>(ty, tx), s>>>(
-                coef, (const R*)p->ll[(lev + 1) & 1], (R*)p->ll[lev & 1], (const R*)p->filt, p->filt_len,
-                mode == 1 ? active : nullptr, lev, L, ny, nx);
+                coef, (const R*)p->ll[(lev + 1) & 1], dst, (const R*)p->filt, p->filt_len,
+                mode == 1 ? active : nullptr, lev, L, ny, nx, stride);
             if ((e = cudaGetLastError())) return e;
         }
     }
-    const int ty = std::min(ST, ny), tx = std::min(ST, nx);
-    dim3 grid((nx + tx - 1) / tx, (ny + ty - 1) / ty, 1);
-    if ((e = ensure_smem(k_idwt_final<R, 0>, syn_smem<R>(ty, tx))) ||
-        (e = ensure_smem(k_idwt_final<R, 1>, syn_smem<R>(ty, tx))))
-        return e;
+    const int ctas = (int)std::min<int64_t>((n / 4 + 255) / 256, (int64_t)p->num_sms * 8);
     if (mode == 0)
-        k_idwt_final<R, 0><<<grid, NT_W, syn_smem<R>(ty, tx), s>>>(coef, (const R*)p->ll[1], out, (const R*)p->filt,
-                                                                   p->filt_len, active, b, L, ny, nx, scale);
+        k_syn_sum<R, 0><<<ctas, 256, 0, s>>>(coef, (const R*)p->synpart, p->filt_len, active, b, n, out, scale);
     else
-        k_idwt_final<R, 1><<<grid, NT_W, syn_smem<R>(ty, tx), s>>>(coef, (const R*)p->ll[1], out, (const R*)p->filt,
-                                                                   p->filt_len, active, b, L, ny, nx, scale);
+        k_syn_sum<R, 1><<<ctas, 256, 0, s>>>(coef, (const R*)p->synpart, p->filt_len, active, b, n, out, scale);
     return cudaGetLastError();
 }
 
