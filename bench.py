@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-operators", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0, help="gridding tile edge (0: the plan's default)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip pd_plan_autotune (16, 32, 64) and plan with --tile (0: the plan's default)")
     ap.add_argument("--cpu-full", type=int, default=0,
                     help="time this many oracle iterations on the full c5 workload (CPU only) and exit")
     return ap.parse_args()
@@ -289,9 +292,16 @@ def run_ours(args):
     uv, blk, x_true, noise = make_inputs(cfg, rank_seed(args.seed, rank))
     d = int(blk.max()) + 1
     b = len(cfg["bases"])
+    tile, tune = args.tile, None
+    if not args.no_autotune and not args.tile:
+        from paper_1610_08895_gb300.api import autotune_tile
+        tile, tune = autotune_tile(n, n, uv, blk, d, kernel_width=cfg["J"], basis_ids=cfg["bases"],
+                                   levels=cfg["levels"], candidates=(16, 32, 64), iters=5)
     plan = Plan(n, n, uv, blk, d, kernel_width=cfg["J"], basis_ids=cfg["bases"], levels=cfg["levels"],
-                precision="f32")
+                precision="f32", tile=tile)
     info = plan.info()
+    if tune is not None:
+        info["autotune_ms_per_iteration"] = {str(k): round(v, 4) for k, v in tune.items()}
     sizes = np.bincount(blk, minlength=d)
     # measurements y = Phi x + n (Phi on the GPU), bounds from the chi-square quantile
     xt = torch.tensor(x_true, dtype=torch.float32, device="cuda")
@@ -389,26 +399,38 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
         st2.close()
 
-    # ---- the same workload with FP64 bulk data (the plain FP64 form, for comparison)
+    # ---- FP64 forms of the same workload: the plain per-block form (the host draws the active
+    # sets and launches each data-fidelity operator once per active block, each sparsity operator
+    # once per active basis) and the batched graph form with FP64 bulk data
     fp64 = None
     if not args.no_fp64:
         plan64 = Plan(n, n, uv, blk, d, kernel_width=cfg["J"], basis_ids=cfg["bases"], levels=cfg["levels"],
-                      precision="f64")
-        st64 = State(plan64)
-        st64.pd_state_set_data(torch.tensor(y_host.astype(np.complex128), device="cuda"), eps)
-        st64.pd_iterate(3, use_graph=True, **kw)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        st64.pd_iterate(args.fp64_steps, use_graph=True, **kw)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1)
-        fp64 = {"value": round(args.fp64_steps / (ms64 / 1e3), 3), "unit": "PD iters/s",
-                "ms_per_step": round(ms64 / args.fp64_steps, 3), "steps": args.fp64_steps,
-                "form": "same kernels and graph with FP64 bulk data (I0 evaluated directly)"}
-        st64.close()
+                      precision="f64", tile=tile)
+        fp64 = {}
+        for form, extra in (("per_block", dict(per_block=True)), ("batched_graph", dict(use_graph=True))):
+            st64 = State(plan64)
+            st64.pd_state_set_data(torch.tensor(y_host.astype(np.complex128), device="cuda"), eps)
+            st64.pd_iterate(2, **extra, **kw)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            st64.pd_iterate(args.fp64_steps, **extra, **kw)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = f0.elapsed_time(f1)
+            fp64[form] = {"value": round(args.fp64_steps / (ms64 / 1e3), 3), "unit": "PD iters/s",
+                          "ms_per_step": round(ms64 / args.fp64_steps, 3), "steps": args.fp64_steps}
+            st64.close()
+        fp64["per_block"]["form"] = ("FP64 throughout; host-drawn active sets; one degridding, ball update, "
+                                     "gridding (per tile colour) launch per active block and one analysis / "
+                                     "synthesis launch set per active basis; eager")
+        fp64["batched_graph"]["form"] = "FP64 bulk data in the batched kernels, one CUDA graph per iteration"
         plan64.close()
+
+    # ---- errors of this run's results against the FP64 oracle on sampled outputs
+    errors = None
+    if rank == 0 and not args.no_cpu_baseline:
+        errors = sampled_errors(cfg, uv, x_true, phix)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -428,7 +450,7 @@ def run_ours(args):
                        "graph": "one CUDA graph per iteration, replayed", "setup_s": round(setup_s, 1),
                        "plan": info},
             "roofline": roofline, "kernels": kernels, "clocks": clk.summary(), "e2e": e2e,
-            "fp64": fp64, "operators": operators, "cpu_baseline": cpu,
+            "fp64": fp64, "operators": operators, "cpu_baseline": cpu, "errors": errors,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -449,6 +471,20 @@ def oracle_problem(cfg, seed):
     prob.y = phix + sn * noise
     prob.eps = EX.epsilon_bounds(sn, [max(len(ix), 1) for ix in prob.block_index])
     return prob
+
+
+def sampled_errors(cfg, uv, x_true, phix_gpu, nsample=20000, seed=7):
+    """Relative error of this run's FP32 Phi x_true against the FP64 oracle at nsample
+    visibilities (the oracle's F Z x in full, its G at the samples only)."""
+    from oracle import measurement as meas
+    geo = meas.Geometry(cfg["n"], cfg["n"], cfg["J"])
+    idx = np.random.default_rng(seed).choice(len(uv), size=nsample, replace=False)
+    ref = geo.degrid(geo.fft(geo.zpad(x_true)), uv[idx])
+    got = phix_gpu.cpu().numpy()[idx].astype(np.complex128)
+    return {"phi_sampled_rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "sample": f"Phi x_true at {nsample} of {len(uv)} visibilities",
+            "parity_tests": "the iterate and operator errors of the -m gpu parity tests are tabulated with "
+                            "the design notes (C1 200 it., C2 500 it., C3, C5 Phi^H full image, C5 iteration)"}
 
 
 def host_cpu():

@@ -395,22 +395,54 @@ extern "C" pd_status pd_plan_info(const pd_plan* p, int32_t* ky, int32_t* kx, do
 }
 
 // ------------------------------------------------------------------ operators
+// Scratch of a batch of operator applications (one launch per pass for the whole batch):
+// the plan's own buffers for one image, otherwise buffers kept by the plan and grown to
+// the largest batch seen (the device is synchronised before the old ones are freed).
+static pd_status ensure_batch(pd_plan* p, int batch, void** t1, void** gb, void** gu) {
+    if (batch == 1) {
+        *t1 = p->t1; *gb = p->gridb; *gu = p->gridu;
+        return PD_OK;
+    }
+    if (batch > p->batch_cap) {
+        CU(cudaDeviceSynchronize());
+        for (void* q : {p->bt1, p->bgb, p->bgu})
+            if (q) {
+                cudaFree(q);
+                p->allocs.erase(std::remove(p->allocs.begin(), p->allocs.end(), q), p->allocs.end());
+            }
+        p->bt1 = p->bgb = p->bgu = nullptr;
+        p->batch_cap = 0;
+        const size_t half = (size_t)(p->g.nx / 4 + 1) * 4;
+        size_t dummy = 0;
+        if (dalloc_bytes(p->allocs, dummy, &p->bt1, batch * half * p->g.ny * p->csz) ||
+            dalloc_bytes(p->allocs, dummy, &p->bgb, batch * half * p->g.Ky * p->csz) ||
+            dalloc_bytes(p->allocs, dummy, &p->bgu, (size_t)batch * p->g.Kx * p->g.Ky * p->csz))
+            return fail(PD_ENOMEM, "batch scratch allocation failed");
+        // the unused slots of the last column panel of the half grids stay zero
+        CU(cudaMemset(p->bt1, 0, batch * half * p->g.ny * p->csz));
+        CU(cudaMemset(p->bgb, 0, batch * half * p->g.Ky * p->csz));
+        p->batch_cap = batch;
+    }
+    *t1 = p->bt1; *gb = p->bgb; *gu = p->bgu;
+    return PD_OK;
+}
+
 template <typename R>
 static pd_status apply_phi_t(pd_plan* p, const void* x, void* y, int batch, cudaStream_t s) {
-    const int64_t N = (int64_t)p->g.nx * p->g.ny;
-    for (int k = 0; k < batch; ++k) {
-        CU(fwd_fft<R>(p, (const R*)x + k * N, (cplx_t<R>*)p->gridb, s));
-        CU(degrid_plain<R>(p, (const cplx_t<R>*)p->gridb, (cplx_t<R>*)y + k * p->M, s));
-    }
+    void *t1, *gb, *gu;
+    pd_status st = ensure_batch(p, batch, &t1, &gb, &gu);
+    if (st != PD_OK) return st;
+    CU(fwd_fft<R>(p, (const R*)x, (cplx_t<R>*)gb, s, batch, (cplx_t<R>*)t1));
+    CU(degrid_plain<R>(p, (const cplx_t<R>*)gb, (cplx_t<R>*)y, s, batch));
     return PD_OK;
 }
 template <typename R>
 static pd_status apply_phi_adj_t(pd_plan* p, const void* y, void* x, int batch, cudaStream_t s) {
-    const int64_t N = (int64_t)p->g.nx * p->g.ny;
-    for (int k = 0; k < batch; ++k) {
-        CU(grid_plain<R>(p, (const cplx_t<R>*)y + k * p->M, (cplx_t<R>*)p->gridu, s));
-        CU(inv_fft<R>(p, (const cplx_t<R>*)p->gridu, (R*)x + k * N, nullptr, s));
-    }
+    void *t1, *gb, *gu;
+    pd_status st = ensure_batch(p, batch, &t1, &gb, &gu);
+    if (st != PD_OK) return st;
+    CU(grid_plain<R>(p, (const cplx_t<R>*)y, (cplx_t<R>*)gu, s, batch));
+    CU(inv_fft<R>(p, (const cplx_t<R>*)gu, (R*)x, nullptr, s, batch, (cplx_t<R>*)t1));
     return PD_OK;
 }
 

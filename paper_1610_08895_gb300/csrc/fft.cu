@@ -141,6 +141,27 @@ __device__ __forceinline__ void fft_smem(cplx_t<R>* s, const cplx_t<R>* __restri
     stages<R, N, 1, SIGN, NSEQ>(s, twK);
 }
 
+// e = threadIdx.x, threadIdx.x + NT, ... < total, with the global loads of UB consecutive
+// steps issued before any of their shared-memory stores (a plain strided loop waits for
+// each load in turn, which leaves these passes bound by one memory latency per step).
+template <int UB, int NT, class Ld, class St>
+__device__ __forceinline__ void batched_loop(int total, const Ld& ld, const St& st) {
+    using V = decltype(ld(0));
+    for (int base = threadIdx.x; base < total; base += UB * NT) {
+        V v[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int e = base + u * NT;
+            if (e < total) v[u] = ld(e);
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int e = base + u * NT;
+            if (e < total) st(e, v[u]);
+        }
+    }
+}
+
 // Rows (pairs) per CTA of the row passes and columns per CTA of the column passes:
 // as many as keep a CTA at 512 threads (so a thread may hold 128 registers), at most 4,
 // at least 1 (the longest transforms then take 1024 threads).
@@ -153,6 +174,9 @@ template <typename R, int N> struct PassShape {
     static constexpr int NT_COLS = 2 * CQ * N / EPT < 32 ? 32 : 2 * CQ * N / EPT;
     static constexpr size_t SMEM_ROWS = (size_t)2 * PAIRS * Shape<R, N>::PN * sizeof(cplx_t<R>);
     static constexpr size_t SMEM_COLS = (size_t)2 * CQ * Shape<R, N>::PN * sizeof(cplx_t<R>);
+    // two CTAs per SM where the threads allow it (the register budget per thread follows)
+    static constexpr int MIN_CTAS_ROWS = NT_ROWS <= 512 ? 2 : 1;
+    static constexpr int MIN_CTAS_COLS = NT_COLS <= 512 ? 2 : 1;
 };
 
 // ---------------------------------------------------------------------------
@@ -161,28 +185,32 @@ template <typename R, int N> struct PassShape {
 // pre-twiddled z for the odd ones. Output: the half spectrum kx = 0 .. nx of each row,
 // X_a[k] = (Z[k] + conj Z[-k]) / 2 and X_b[k] = (Z[k] - conj Z[-k]) / (2i), into t1.
 template <typename R, int N>
-__global__ void __launch_bounds__(PassShape<R, N>::NT_ROWS) k_fwd_rows(
+__global__ void __launch_bounds__(PassShape<R, N>::NT_ROWS, PassShape<R, N>::MIN_CTAS_ROWS) k_fwd_rows(
     const R* __restrict__ x, cplx_t<R>* __restrict__ t1, const R* __restrict__ cx, const R* __restrict__ cy,
-    const cplx_t<R>* __restrict__ twx, int ny) {
+    const cplx_t<R>* __restrict__ twx, int ny, int64_t t1_stride) {
     using C2 = cplx_t<R>;
     using S = Shape<R, N>;
     using P = PassShape<R, N>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* s = reinterpret_cast<C2*>(smraw);
+    x += (int64_t)blockIdx.y * ny * N;                 // image blockIdx.y of a batch
+    t1 += (int64_t)blockIdx.y * t1_stride;
     constexpr int NT = P::NT_ROWS, Kx = 2 * N;
     const int iy0 = blockIdx.x * 2 * P::PAIRS;
-    for (int e = threadIdx.x; e < P::PAIRS * N; e += NT) {
+    struct In { R va, vb; C2 w; };
+    batched_loop<4, NT>(P::PAIRS * N, [&](int e) {
         const int pr = e / N, ix = e % N;
         const int a = iy0 + 2 * pr;
         const R c = cx[ix];
-        const R va = x[(int64_t)a * N + ix] * c * cy[a];
-        const R vb = x[(int64_t)(a + 1) * N + ix] * c * cy[a + 1];
         const int lc = ix - N / 2;
-        const int m = padi<R>(lc & (N - 1));
-        const C2 w = __ldg(&twx[lc & (Kx - 1)]);
-        s[(2 * pr) * S::PN + m] = mk<C2>(va, vb);
-        s[(2 * pr + 1) * S::PN + m] = mk<C2>(va * w.x - vb * w.y, va * w.y + vb * w.x);
-    }
+        return In{x[(int64_t)a * N + ix] * c * cy[a], x[(int64_t)(a + 1) * N + ix] * c * cy[a + 1],
+                  __ldg(&twx[lc & (Kx - 1)])};
+    }, [&](int e, const In& v) {
+        const int pr = e / N, ix = e % N;
+        const int m = padi<R>((ix - N / 2) & (N - 1));
+        s[(2 * pr) * S::PN + m] = mk<C2>(v.va, v.vb);
+        s[(2 * pr + 1) * S::PN + m] = mk<C2>(v.va * v.w.x - v.vb * v.w.y, v.va * v.w.y + v.vb * v.w.x);
+    });
     __syncthreads();
     fft_smem<R, N, -1, 2 * P::PAIRS>(s, twx);
     // outputs ordered (panel, row, slot): 2 PAIRS rows x 4 slots of a panel are contiguous
@@ -213,24 +241,29 @@ __global__ void __launch_bounds__(PassShape<R, N>::NT_ROWS) k_fwd_rows(
 // Forward column pass (F along y) of CQ half-grid columns of one panel: sequence qq holds
 // column q0 + qq for the even outputs, CQ + qq the pre-twiddled column for the odd ones.
 template <typename R, int N>
-__global__ void __launch_bounds__(PassShape<R, N>::NT_COLS) k_fwd_cols(
-    const cplx_t<R>* __restrict__ t1, cplx_t<R>* __restrict__ gb, const cplx_t<R>* __restrict__ twy) {
+__global__ void __launch_bounds__(PassShape<R, N>::NT_COLS, PassShape<R, N>::MIN_CTAS_COLS) k_fwd_cols(
+    const cplx_t<R>* __restrict__ t1, cplx_t<R>* __restrict__ gb, const cplx_t<R>* __restrict__ twy,
+    int64_t t1_stride, int64_t gb_stride) {
     using C2 = cplx_t<R>;
     using S = Shape<R, N>;
     using P = PassShape<R, N>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* s = reinterpret_cast<C2*>(smraw);
+    t1 += (int64_t)blockIdx.y * t1_stride;
+    gb += (int64_t)blockIdx.y * gb_stride;
     constexpr int NT = P::NT_COLS, CQ = P::CQ, Ky = 2 * N, PER = 4 / CQ;
     const int p = blockIdx.x / PER, q0 = (blockIdx.x % PER) * CQ;
     const C2* src = t1 + (int64_t)p * N * 4 + q0;
-    for (int e = threadIdx.x; e < N * CQ; e += NT) {
+    struct In { C2 val, w; };
+    batched_loop<4, NT>(N * CQ, [&](int e) {
         const int iy = e / CQ, qq = e % CQ;
-        const C2 val = src[iy * 4 + qq];
-        const int lc = iy - N / 2;
-        const int m = padi<R>(lc & (N - 1));
-        s[qq * S::PN + m] = val;
-        s[(CQ + qq) * S::PN + m] = cmul(val, __ldg(&twy[lc & (Ky - 1)]));
-    }
+        return In{src[iy * 4 + qq], __ldg(&twy[(iy - N / 2) & (Ky - 1)])};
+    }, [&](int e, const In& v) {
+        const int iy = e / CQ, qq = e % CQ;
+        const int m = padi<R>((iy - N / 2) & (N - 1));
+        s[qq * S::PN + m] = v.val;
+        s[(CQ + qq) * S::PN + m] = cmul(v.val, v.w);
+    });
     __syncthreads();
     fft_smem<R, N, -1, 2 * CQ>(s, twy);
     C2* dst = gb + (int64_t)p * Ky * 4 + q0;
@@ -245,23 +278,29 @@ __global__ void __launch_bounds__(PassShape<R, N>::NT_COLS) k_fwd_cols(
 // even inputs in sequence qq and odd inputs in CQ + qq; the cropped row iy is
 // E[m] + conj(W_2ny^lc) O[m] with lc = iy - ny/2, m = lc mod ny.
 template <typename R, int N>
-__global__ void __launch_bounds__(PassShape<R, N>::NT_COLS) k_inv_cols(
-    const cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ t1, const cplx_t<R>* __restrict__ twy, int Kx) {
+__global__ void __launch_bounds__(PassShape<R, N>::NT_COLS, PassShape<R, N>::MIN_CTAS_COLS) k_inv_cols(
+    const cplx_t<R>* __restrict__ U, cplx_t<R>* __restrict__ t1, const cplx_t<R>* __restrict__ twy, int Kx,
+    int64_t t1_stride) {
     using C2 = cplx_t<R>;
     using S = Shape<R, N>;
     using P = PassShape<R, N>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* s = reinterpret_cast<C2*>(smraw);
+    U += (int64_t)blockIdx.y * Kx * 2 * N;
+    t1 += (int64_t)blockIdx.y * t1_stride;
     constexpr int NT = P::NT_COLS, CQ = P::CQ, Ky = 2 * N, PER = 4 / CQ;
     const int p = blockIdx.x / PER, q0 = (blockIdx.x % PER) * CQ;
-    for (int e = threadIdx.x; e < Ky * CQ; e += NT) {
+    struct In { C2 u, um; };
+    batched_loop<4, NT>(Ky * CQ, [&](int e) {
         const int ky = e / CQ, qq = e % CQ;
         const int kx = 4 * p + q0 + qq;
         const int mkx = (Kx - kx) & (Kx - 1), mky = (Ky - ky) & (Ky - 1);
-        const C2 u = U[panel_off(ky, kx, Ky)], um = U[panel_off(mky, mkx, Ky)];
+        return In{U[panel_off(ky, kx, Ky)], U[panel_off(mky, mkx, Ky)]};
+    }, [&](int e, const In& v) {
+        const int ky = e / CQ, qq = e % CQ;
         s[((ky & 1) * CQ + qq) * S::PN + padi<R>(ky >> 1)] =
-            mk<C2>(R(0.5) * (u.x + um.x), R(0.5) * (u.y - um.y));
-    }
+            mk<C2>(R(0.5) * (v.u.x + v.um.x), R(0.5) * (v.u.y - v.um.y));
+    });
     __syncthreads();
     fft_smem<R, N, +1, 2 * CQ>(s, twy);
     C2* dst = t1 + (int64_t)p * N * 4 + q0;
@@ -279,28 +318,35 @@ __global__ void __launch_bounds__(PassShape<R, N>::NT_COLS) k_inv_cols(
 // Mode 0 stores Re(Phi^H)-type output; mode 1 runs the primal update of Alg. 1 steps
 // 17-18 as epilogue with per-CTA FP64 partial norms.
 template <typename R, int N>
-__global__ void __launch_bounds__(PassShape<R, N>::NT_ROWS) k_inv_rows(
+__global__ void __launch_bounds__(PassShape<R, N>::NT_ROWS, PassShape<R, N>::MIN_CTAS_ROWS) k_inv_rows(
     const cplx_t<R>* __restrict__ t1, R* __restrict__ out, const R* __restrict__ cx, const R* __restrict__ cy,
     const cplx_t<R>* __restrict__ twx, int ny, int mode, R tau, R sigma, R varsigma, R* __restrict__ xs,
-    R* __restrict__ xt, const R* __restrict__ st_, double* __restrict__ part) {
+    R* __restrict__ xt, const R* __restrict__ st_, double* __restrict__ part, int64_t t1_stride) {
     using C2 = cplx_t<R>;
     using S = Shape<R, N>;
     using P = PassShape<R, N>;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[32];
     C2* s = reinterpret_cast<C2*>(smraw);
+    t1 += (int64_t)blockIdx.y * t1_stride;             // image blockIdx.y of a batch (mode 0)
+    if (mode == 0) out += (int64_t)blockIdx.y * ny * N;
     constexpr int NT = P::NT_ROWS, Kx = 2 * N, NPH = N / 4 + 1;
     const int iy0 = blockIdx.x * 2 * P::PAIRS;
-    for (int e = threadIdx.x; e < NPH * P::PAIRS * 4; e += NT) {
+    struct In { C2 ta, tb; };
+    batched_loop<4, NT>(NPH * P::PAIRS * 4, [&](int e) {
+        const int q = e & 3, pr = (e >> 2) % P::PAIRS, pp = (e >> 2) / P::PAIRS;
+        const int a = iy0 + 2 * pr;
+        In v;
+        if (4 * pp + q <= N) { v.ta = t1[((int64_t)pp * ny + a) * 4 + q]; v.tb = t1[((int64_t)pp * ny + a + 1) * 4 + q]; }
+        return v;
+    }, [&](int e, const In& v) {
         const int q = e & 3, pr = (e >> 2) % P::PAIRS, pp = (e >> 2) / P::PAIRS;
         const int k = 4 * pp + q;
-        if (k > N) continue;
-        const int a = iy0 + 2 * pr;
-        const C2 ta = t1[((int64_t)pp * ny + a) * 4 + q], tb = t1[((int64_t)pp * ny + a + 1) * 4 + q];
+        if (k > N) return;
         C2* seq = s + (2 * pr + (k & 1)) * S::PN;
-        seq[padi<R>(k >> 1)] = mk<C2>(ta.x - tb.y, ta.y + tb.x);
-        if (k != 0 && k != N) seq[padi<R>((Kx - k) >> 1)] = mk<C2>(ta.x + tb.y, tb.x - ta.y);
-    }
+        seq[padi<R>(k >> 1)] = mk<C2>(v.ta.x - v.tb.y, v.ta.y + v.tb.x);
+        if (k != 0 && k != N) seq[padi<R>((Kx - k) >> 1)] = mk<C2>(v.ta.x + v.tb.y, v.tb.x - v.ta.y);
+    });
     __syncthreads();
     fft_smem<R, N, +1, 2 * P::PAIRS>(s, twx);
     R adx = R(0), ax = R(0);
@@ -356,48 +402,54 @@ __global__ void __launch_bounds__(PassShape<R, N>::NT_ROWS) k_inv_rows(
         default: return cudaErrorInvalidValue;                   \
     }
 
+// complex elements of one image's half-grid intermediates: t1 (ny rows) and F Z x (Ky rows)
+static int64_t t1_elems(const pd_plan* p) { return (int64_t)(p->g.nx / 4 + 1) * 4 * p->g.ny; }
+static int64_t gb_elems(const pd_plan* p) { return (int64_t)(p->g.nx / 4 + 1) * 4 * p->g.Ky; }
+
 template <typename R, int N>
-static cudaError_t launch_fwd_rows(const pd_plan* p, const R* x, cplx_t<R>* t1, cudaStream_t s) {
+static cudaError_t launch_fwd_rows(const pd_plan* p, const R* x, cplx_t<R>* t1, int batch, cudaStream_t s) {
     using P = PassShape<R, N>;
     cudaError_t e;
     if ((e = ensure_smem(k_fwd_rows<R, N>, P::SMEM_ROWS))) return e;
-    k_fwd_rows<R, N><<<p->g.ny / (2 * P::PAIRS), P::NT_ROWS, P::SMEM_ROWS, s>>>(
-        x, t1, (const R*)p->cx, (const R*)p->cy, (const cplx_t<R>*)p->twx, p->g.ny);
+    k_fwd_rows<R, N><<<dim3(p->g.ny / (2 * P::PAIRS), batch), P::NT_ROWS, P::SMEM_ROWS, s>>>(
+        x, t1, (const R*)p->cx, (const R*)p->cy, (const cplx_t<R>*)p->twx, p->g.ny, t1_elems(p));
     return cudaGetLastError();
 }
 template <typename R, int N>
-static cudaError_t launch_fwd_cols(const pd_plan* p, const cplx_t<R>* t1, cplx_t<R>* gb, cudaStream_t s) {
+static cudaError_t launch_fwd_cols(const pd_plan* p, const cplx_t<R>* t1, cplx_t<R>* gb, int batch,
+                                   cudaStream_t s) {
     using P = PassShape<R, N>;
     cudaError_t e;
     if ((e = ensure_smem(k_fwd_cols<R, N>, P::SMEM_COLS))) return e;
-    k_fwd_cols<R, N><<<(p->g.nx / 4 + 1) * (4 / P::CQ), P::NT_COLS, P::SMEM_COLS, s>>>(
-        t1, gb, (const cplx_t<R>*)p->twy);
+    k_fwd_cols<R, N><<<dim3((p->g.nx / 4 + 1) * (4 / P::CQ), batch), P::NT_COLS, P::SMEM_COLS, s>>>(
+        t1, gb, (const cplx_t<R>*)p->twy, t1_elems(p), gb_elems(p));
     return cudaGetLastError();
 }
 template <typename R, int N>
-static cudaError_t launch_inv_cols(const pd_plan* p, const cplx_t<R>* U, cplx_t<R>* t1, cudaStream_t s) {
+static cudaError_t launch_inv_cols(const pd_plan* p, const cplx_t<R>* U, cplx_t<R>* t1, int batch,
+                                   cudaStream_t s) {
     using P = PassShape<R, N>;
     cudaError_t e;
     if ((e = ensure_smem(k_inv_cols<R, N>, P::SMEM_COLS))) return e;
-    k_inv_cols<R, N><<<(p->g.nx / 4 + 1) * (4 / P::CQ), P::NT_COLS, P::SMEM_COLS, s>>>(
-        U, t1, (const cplx_t<R>*)p->twy, p->g.Kx);
+    k_inv_cols<R, N><<<dim3((p->g.nx / 4 + 1) * (4 / P::CQ), batch), P::NT_COLS, P::SMEM_COLS, s>>>(
+        U, t1, (const cplx_t<R>*)p->twy, p->g.Kx, t1_elems(p));
     return cudaGetLastError();
 }
 template <typename R, int N>
-static cudaError_t launch_inv_rows(const pd_plan* p, const cplx_t<R>* t1, R* out, const PrimalArgs* pa,
+static cudaError_t launch_inv_rows(const pd_plan* p, const cplx_t<R>* t1, R* out, const PrimalArgs* pa, int batch,
                                    cudaStream_t s) {
     using P = PassShape<R, N>;
     cudaError_t e;
     if ((e = ensure_smem(k_inv_rows<R, N>, P::SMEM_ROWS))) return e;
     const int ctas = p->g.ny / (2 * P::PAIRS);
     if (pa == nullptr)
-        k_inv_rows<R, N><<<ctas, P::NT_ROWS, P::SMEM_ROWS, s>>>(t1, out, (const R*)p->cx, (const R*)p->cy,
-                                                               (const cplx_t<R>*)p->twx, p->g.ny, 0, R(0), R(0),
-                                                               R(0), nullptr, nullptr, nullptr, nullptr);
+        k_inv_rows<R, N><<<dim3(ctas, batch), P::NT_ROWS, P::SMEM_ROWS, s>>>(
+            t1, out, (const R*)p->cx, (const R*)p->cy, (const cplx_t<R>*)p->twx, p->g.ny, 0, R(0), R(0), R(0),
+            nullptr, nullptr, nullptr, nullptr, t1_elems(p));
     else
         k_inv_rows<R, N><<<ctas, P::NT_ROWS, P::SMEM_ROWS, s>>>(
             t1, nullptr, (const R*)p->cx, (const R*)p->cy, (const cplx_t<R>*)p->twx, p->g.ny, 1, (R)pa->tau,
-            (R)pa->sigma, (R)pa->varsigma, (R*)pa->x, (R*)pa->xt, (const R*)pa->st, pa->part);
+            (R)pa->sigma, (R)pa->varsigma, (R*)pa->x, (R*)pa->xt, (const R*)pa->st, pa->part, t1_elems(p));
     return cudaGetLastError();
 }
 
@@ -414,36 +466,39 @@ int inv_rows_ctas(const pd_plan* p) {
 }
 
 template <typename R>
-cudaError_t fwd_fft(const pd_plan* p, const R* x, cplx_t<R>* grid, cudaStream_t s) {
+cudaError_t fwd_fft(const pd_plan* p, const R* x, cplx_t<R>* grid, cudaStream_t s, int batch, cplx_t<R>* t1) {
     cudaError_t e = cudaSuccess;
-    cplx_t<R>* t1 = (cplx_t<R>*)p->t1;
+    if (!t1) t1 = (cplx_t<R>*)p->t1;
     prof_mark(PH_FWD_ROWS, 0, s);
-    PD_N_DISPATCH(p->g.nx, (e = launch_fwd_rows<R, NN>(p, x, t1, s)));
+    PD_N_DISPATCH(p->g.nx, (e = launch_fwd_rows<R, NN>(p, x, t1, batch, s)));
     prof_mark(PH_FWD_ROWS, 1, s);
     if (e) return e;
     prof_mark(PH_FWD_COLS, 0, s);
-    PD_N_DISPATCH(p->g.ny, (e = launch_fwd_cols<R, NN>(p, t1, grid, s)));
+    PD_N_DISPATCH(p->g.ny, (e = launch_fwd_cols<R, NN>(p, t1, grid, batch, s)));
     prof_mark(PH_FWD_COLS, 1, s);
     return e;
 }
 
 template <typename R>
-cudaError_t inv_fft(const pd_plan* p, const cplx_t<R>* grid, R* out, const PrimalArgs* pa, cudaStream_t s) {
+cudaError_t inv_fft(const pd_plan* p, const cplx_t<R>* grid, R* out, const PrimalArgs* pa, cudaStream_t s, int batch,
+                    cplx_t<R>* t1) {
     cudaError_t e = cudaSuccess;
-    cplx_t<R>* t1 = (cplx_t<R>*)p->t1;
+    if (!t1) t1 = (cplx_t<R>*)p->t1;
     prof_mark(PH_INV_COLS, 0, s);
-    PD_N_DISPATCH(p->g.ny, (e = launch_inv_cols<R, NN>(p, grid, t1, s)));
+    PD_N_DISPATCH(p->g.ny, (e = launch_inv_cols<R, NN>(p, grid, t1, batch, s)));
     prof_mark(PH_INV_COLS, 1, s);
     if (e) return e;
     prof_mark(PH_INV_ROWS, 0, s);
-    PD_N_DISPATCH(p->g.nx, (e = launch_inv_rows<R, NN>(p, t1, out, pa, s)));
+    PD_N_DISPATCH(p->g.nx, (e = launch_inv_rows<R, NN>(p, t1, out, pa, batch, s)));
     prof_mark(PH_INV_ROWS, 1, s);
     return e;
 }
 
-template cudaError_t fwd_fft<float>(const pd_plan*, const float*, float2*, cudaStream_t);
-template cudaError_t fwd_fft<double>(const pd_plan*, const double*, double2*, cudaStream_t);
-template cudaError_t inv_fft<float>(const pd_plan*, const float2*, float*, const PrimalArgs*, cudaStream_t);
-template cudaError_t inv_fft<double>(const pd_plan*, const double2*, double*, const PrimalArgs*, cudaStream_t);
+template cudaError_t fwd_fft<float>(const pd_plan*, const float*, float2*, cudaStream_t, int, float2*);
+template cudaError_t fwd_fft<double>(const pd_plan*, const double*, double2*, cudaStream_t, int, double2*);
+template cudaError_t inv_fft<float>(const pd_plan*, const float2*, float*, const PrimalArgs*, cudaStream_t, int,
+                                    float2*);
+template cudaError_t inv_fft<double>(const pd_plan*, const double2*, double*, const PrimalArgs*, cudaStream_t, int,
+                                     double2*);
 
 }  // namespace pdgb

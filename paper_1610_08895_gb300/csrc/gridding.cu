@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                                                 const int32_t* __restrict__ active, const int32_t* __restrict__ list,
                                                 const int32_t* __restrict__ count, double* __restrict__ seg_part,
                                                 int max_segs, Geo g, R two_over_j, R beta, const KbPoly kp,
-                                                int* __restrict__ next_tile) {
+                                                int* __restrict__ next_tile, int batch, int64_t gstride,
+                                                int64_t ostride) {
     using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
     // FP32: the window twice, row stride EP (even), the second copy shifted left by one
@@ -149,19 +150,37 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
         if (threadIdx.x == 0) tile_s = atomicAdd(next_tile, 1);
         __syncthreads();
         const int w = tile_s;
-        if (w >= n) break;
-        const int t = list[w];
+        if (w >= n * batch) break;
+        // work item w: tile w / batch of the list for image w mod batch (a batch of plain
+        // applications; the heaviest tiles of every image come first)
+        const int t = list[w / batch], img = w % batch;
+        const cplx_t<R>* gimg = grid + (int64_t)img * gstride;
+        cplx_t<R>* oimg = MODE == 0 ? out + (int64_t)img * ostride : out;
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
         const int oy = ty * T, ox = tx * T;
         const int seg0 = tile_seg_start[t], nseg_t = tile_seg_start[t + 1] - seg0;
         list_active_segments(seg0, nseg_t, seg_block, MODE == 1 ? active : nullptr, seg_start, act_seg, act_pre,
                              &nact_s);
-        for (int i = threadIdx.x; i < E * E; i += blockDim.x) {
-            const int ey = i / E, ex = i - ey * E;
-            const int ky = (oy - H + ey) & (g.Ky - 1), kx = (ox - H + ex) & (g.Kx - 1);
-            const C2 gv = half_grid_at(grid, ky, kx, g);
-            win[ey * EP + ex] = gv;
-            if (PAIRS && ex > 0) win[E * EP + ey * EP + ex - 1] = gv;
+        // the window, four cells' loads in flight per thread
+        for (int i0 = threadIdx.x; i0 < E * E; i0 += 4 * (int)blockDim.x) {
+            C2 gv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * (int)blockDim.x;
+                if (i < E * E) {
+                    const int ey = i / E, ex = i - ey * E;
+                    gv[u] = half_grid_at(gimg, (oy - H + ey) & (g.Ky - 1), (ox - H + ex) & (g.Kx - 1), g);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * (int)blockDim.x;
+                if (i < E * E) {
+                    const int ey = i / E, ex = i - ey * E;
+                    win[ey * EP + ex] = gv[u];
+                    if (PAIRS && ex > 0) win[E * EP + ey * EP + ex - 1] = gv[u];
+                }
+            }
         }
         if (MODE == 1)
             for (int i = threadIdx.x; i < 16 * nseg_t; i += blockDim.x) part[i] = 0.0;
@@ -169,17 +188,33 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
         const int nact = nact_s, total = act_pre[nact];
         double* mypart = part + 2 * nseg_t * warp;
         int j = 0;   // segment cursor: positions only grow, so it only moves forward
+        // the inputs of a thread's next point are loaded while the current one is computed
+        struct Pt { int m, js, c; R fx, fy; C2 yy, vv; };
+        auto load_pt = [&](int pos) {
+            Pt q;
+            while (act_pre[j + 1] <= pos) ++j;
+            q.js = j;
+            q.m = seg_start[act_seg[j]] + pos - act_pre[j];
+            q.fx = fxs[q.m];
+            q.fy = fys[q.m];
+            q.c = cell[q.m];
+            if (MODE == 1) { q.yy = y[q.m]; q.vv = v[q.m]; }
+            return q;
+        };
+        Pt cur{};
+        if ((int)threadIdx.x < total) cur = load_pt(threadIdx.x);
         for (int base = 0; base < total; base += blockDim.x) {
             const int pos = base + threadIdx.x;
             const bool ok = pos < total;
+            Pt nxt{};
+            if (pos + (int)blockDim.x < total) nxt = load_pt(pos + blockDim.x);
             R ar = R(0), ad = R(0);     // squares in the working precision (exact for FP64)
             if (ok) {
-                while (act_pre[j + 1] <= pos) ++j;
-                const int m = seg_start[act_seg[j]] + pos - act_pre[j];
+                const int m = cur.m;
                 R wx[J], wy[J];
-                kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
-                kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
-                const int c = cell[m];
+                kb_taps<R, J>(cur.fx, wx, two_over_j, beta, kp);
+                kb_taps<R, J>(cur.fy, wy, two_over_j, beta, kp);
+                const int c = cur.c;
                 const int r0 = (c >> 16) - oy, c0 = (c & 0xFFFF) - ox;   // footprint origin in the window
                 R sx = 0, sy = 0;
                 if constexpr (PAIRS) {
@@ -213,17 +248,18 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                     }
                 }
                 if (MODE == 0) {
-                    out[perm[m]] = mk<C2>(sx, sy);
+                    oimg[perm[m]] = mk<C2>(sx, sy);
                 } else {
-                    const C2 yy = y[m], vv = v[m];
-                    const R dx = sx - yy.x, dy = sy - yy.y;
-                    const C2 r = mk<C2>(vv.x + dx, vv.y + dy);
+                    const R dx = sx - cur.yy.x, dy = sy - cur.yy.y;
+                    const C2 r = mk<C2>(cur.vv.x + dx, cur.vv.y + dy);
                     rbuf[m] = r;
                     ar = r.x * r.x + r.y * r.y;
                     ad = dx * dx + dy * dy;
                 }
             }
-            if (MODE == 1) warp_seg_add(ok, j, ar, ad, mypart);
+            const int jcur = cur.js;
+            cur = nxt;
+            if (MODE == 1) warp_seg_add(ok, jcur, ar, ad, mypart);
         }
         __syncthreads();
         if (MODE == 1) {
@@ -461,7 +497,7 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
     const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_block,
     const int32_t* __restrict__ tile_seg_start, const int32_t* __restrict__ list, const int32_t* __restrict__ count,
     cplx_t<R>* __restrict__ U, int max_segs, Geo g, R two_over_j, R beta, const KbPoly kp,
-    int* __restrict__ next_tile) {
+    int* __restrict__ next_tile, int batch, int64_t istride, int64_t ustride) {
     static_assert(J <= 8 && J % 2 == 0, "class ownership needs J <= 8");
     using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -491,8 +527,11 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
         if (threadIdx.x == 0) tile_s = atomicAdd(next_tile, 1);
         __syncthreads();
         const int w = tile_s;
-        if (w >= n) break;
-        const int t = list[w];
+        if (w >= n * batch) break;
+        // work item w: tile w / batch of the list for image w mod batch (plain gridding of a batch)
+        const int t = list[w / batch], img = w % batch;
+        const cplx_t<R>* simg = MODE == 0 ? src + (int64_t)img * istride : src;
+        cplx_t<R>* Uimg = U + (int64_t)img * ustride;
         const int ty = t / g.ntx, tx = t - ty * g.ntx;
         const int oy = ty * T, ox = tx * T;
         const int seg0 = tile_seg_start[t], nseg_t = tile_seg_start[t + 1] - seg0;
@@ -516,8 +555,8 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
         GridIn<R> in{};
         int chunk = warp;
         if (chunk < nchunk && chunk * 32 + lane < total)
-            grid_load<R, MODE>(in, chunk * 32 + lane, j, act_pre, act_start, act_scale, src, rbuf, v, cell, fxs, fys,
-                               perm);
+            grid_load<R, MODE>(in, chunk * 32 + lane, j, act_pre, act_start, act_scale, simg, rbuf, v, cell, fxs,
+                               fys, perm);
         for (; chunk < nchunk; chunk += GW_WARPS) {
             const int fill = min(32, total - chunk * 32);
             if (lane < fill) {
@@ -552,8 +591,8 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
             // the next chunk's loads go out now and land while this one is accumulated
             const int nxt = chunk + GW_WARPS;
             if (nxt < nchunk && nxt * 32 + lane < total)
-                grid_load<R, MODE>(in, nxt * 32 + lane, j, act_pre, act_start, act_scale, src, rbuf, v, cell, fxs,
-                                   fys, perm);
+                grid_load<R, MODE>(in, nxt * 32 + lane, j, act_pre, act_start, act_scale, simg, rbuf, v, cell,
+                                   fxs, fys, perm);
             __syncwarp();
             // runs of consecutive points with the same super-row: one set of running sums
             // per run, added to the window at its end
@@ -565,22 +604,32 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
                 starts &= starts - 1;
                 const int q1 = starts ? __ffs(starts) - 1 : fill;
                 const int key = __shfl_sync(0xffffffffu, myk, q0);
-                C2 lo0 = mk<C2>(R(0), R(0)), hi0 = lo0, lo1 = lo0, hi1 = lo0;
-                C2 ry = rrec[q0 * GW_RREC + lcy];
-                R wl0, wh0, wl1, wh1;
-                ld4(crec + q0 * GW_CREC + 2 * lcx, wl0, wh0, wl1, wh1);
-                for (int q = q0; q < q1; ++q) {
-                    C2 ryn = ry;
-                    R nl0 = wl0, nh0 = wh0, nl1 = wl1, nh1 = wh1;
-                    if (q + 1 < q1) {
-                        ryn = rrec[(q + 1) * GW_RREC + lcy];
-                        ld4(crec + (q + 1) * GW_CREC + 2 * lcx, nl0, nh0, nl1, nh1);
-                    }
-                    lo0.x += wl0 * ry.x; lo0.y += wl0 * ry.y;
-                    hi0.x += wh0 * ry.x; hi0.y += wh0 * ry.y;
-                    lo1.x += wl1 * ry.x; lo1.y += wl1 * ry.y;
-                    hi1.x += wh1 * ry.x; hi1.y += wh1 * ry.y;
-                    ry = ryn; wl0 = nl0; wh0 = nh0; wl1 = nl1; wh1 = nh1;
+                // the run's first point starts the running sums, the others add to them two at a time
+                C2 lo0, hi0, lo1, hi1;
+                {
+                    const C2 ry = rrec[q0 * GW_RREC + lcy];
+                    R wl0, wh0, wl1, wh1;
+                    ld4(crec + q0 * GW_CREC + 2 * lcx, wl0, wh0, wl1, wh1);
+                    lo0 = mk<C2>(wl0 * ry.x, wl0 * ry.y); hi0 = mk<C2>(wh0 * ry.x, wh0 * ry.y);
+                    lo1 = mk<C2>(wl1 * ry.x, wl1 * ry.y); hi1 = mk<C2>(wh1 * ry.x, wh1 * ry.y);
+                }
+                int q = q0 + 1;
+                for (; q + 1 < q1; q += 2) {
+                    const C2 ra = rrec[q * GW_RREC + lcy], rb = rrec[(q + 1) * GW_RREC + lcy];
+                    R al0, ah0, al1, ah1, bl0, bh0, bl1, bh1;
+                    ld4(crec + q * GW_CREC + 2 * lcx, al0, ah0, al1, ah1);
+                    ld4(crec + (q + 1) * GW_CREC + 2 * lcx, bl0, bh0, bl1, bh1);
+                    lo0.x += al0 * ra.x; lo0.y += al0 * ra.y; hi0.x += ah0 * ra.x; hi0.y += ah0 * ra.y;
+                    lo1.x += al1 * ra.x; lo1.y += al1 * ra.y; hi1.x += ah1 * ra.x; hi1.y += ah1 * ra.y;
+                    lo0.x += bl0 * rb.x; lo0.y += bl0 * rb.y; hi0.x += bh0 * rb.x; hi0.y += bh0 * rb.y;
+                    lo1.x += bl1 * rb.x; lo1.y += bl1 * rb.y; hi1.x += bh1 * rb.x; hi1.y += bh1 * rb.y;
+                }
+                if (q < q1) {
+                    const C2 ry = rrec[q * GW_RREC + lcy];
+                    R wl0, wh0, wl1, wh1;
+                    ld4(crec + q * GW_CREC + 2 * lcx, wl0, wh0, wl1, wh1);
+                    lo0.x += wl0 * ry.x; lo0.y += wl0 * ry.y; hi0.x += wh0 * ry.x; hi0.y += wh0 * ry.y;
+                    lo1.x += wl1 * ry.x; lo1.y += wl1 * ry.y; hi1.x += wh1 * ry.x; hi1.y += wh1 * ry.y;
                 }
                 const int r0 = key >> 16, g0 = key & 0xFFFF;
                 C2* cp = win + (r0 + ((lcy - r0) & 7)) * EP + g0 + lcx;
@@ -591,7 +640,7 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
         }
         __syncthreads();
         // U += the sum of the warps' windows (tile and halo)
-        add_window<R>(U, oy, ox, g, [&](int ey, int ex) {
+        add_window<R>(Uimg, oy, ox, g, [&](int ey, int ex) {
             const int kk = ey * EP + ex;
             C2 sum = wins[kk];
 #pragma unroll
@@ -618,7 +667,8 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
 
 template <typename R, int J, int MODE>
 static cudaError_t launch_degrid(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out, const DualArgs* a,
-                                 const int32_t* tiles, const int32_t* count, int ctas, cudaStream_t s) {
+                                 const int32_t* tiles, const int32_t* count, int ctas, cudaStream_t s,
+                                 int batch = 1) {
     const Geo& g = p->g;
     const int ms = std::max(p->max_tile_segs, 1);
     const size_t win = sizeof(R) == 4 ? (size_t)2 * g.ext * ((g.ext + 2) & ~1) : (size_t)g.ext * g.ext;
@@ -636,16 +686,16 @@ static cudaError_t launch_degrid(const pd_plan* p, const cplx_t<R>* grid, cplx_t
         grid, out, a ? (const cplx_t<R>*)a->y : nullptr, a ? (const cplx_t<R>*)a->v : nullptr,
         (cplx_t<R>*)p->rbuf, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start, p->seg_block,
         p->tile_seg_start, a ? a->block_active : nullptr, tiles, count, p->seg_part, ms, g, R(2.0 / g.J),
-        R(g.beta), p->kbpoly, p->sched + 4);
+        R(g.beta), p->kbpoly, p->sched + 4, batch, (int64_t)(g.nx / 4 + 1) * 4 * g.Ky, (int64_t)p->M);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t degrid_plain(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out_user, cudaStream_t s) {
-    const int ctas = std::min(p->g.ntiles, p->num_sms * 8);
+cudaError_t degrid_plain(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out_user, cudaStream_t s, int batch) {
+    const int ctas = (int)std::min<int64_t>((int64_t)p->g.ntiles * batch, (int64_t)p->num_sms * 8);
     cudaError_t e = cudaSuccess;
     PD_J_DISPATCH(p->g.J, (e = launch_degrid<R, JJ, 0>(p, grid, out_user, nullptr, p->tile_order,
-                                                        p->counts_all + 1, ctas, s)));
+                                                        p->counts_all + 1, ctas, s, batch)));
     return e;
 }
 
@@ -684,7 +734,7 @@ cudaError_t degrid_res_norms(const pd_plan* p, const cplx_t<R>* grid, const cplx
 
 template <typename R, int J, int MODE>
 static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const DualArgs* a, const int32_t* tiles,
-                                 const int32_t* count, cplx_t<R>* U, int* next_tile, cudaStream_t s) {
+                                 const int32_t* count, cplx_t<R>* U, int* next_tile, cudaStream_t s, int batch) {
     const Geo& g = p->g;
     const int ms = std::max(p->max_tile_segs, 1);
     const size_t lists = (size_t)(2 * ms + 1) * sizeof(int);
@@ -704,14 +754,17 @@ static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const D
             ctas8 = std::min(ctas8, per_sm * p->num_sms);
         k_grid8w<R, J, MODE><<<ctas8, GW_WARPS * 32, smem8, s>>>(
             src, rb, vv, (const R*)p->blk_scale, act, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm,
-            p->seg_start, p->seg_block, p->tile_seg_start, tiles, count, U, ms, g, toj, beta, p->kbpoly, next_tile);
+            p->seg_start, p->seg_block, p->tile_seg_start, tiles, count, U, ms, g, toj, beta, p->kbpoly, next_tile,
+            batch, (int64_t)p->M, (int64_t)g.Kx * g.Ky);
     } else {
         const size_t smem = (size_t)2 * g.ext * g.ext * sizeof(R) + lists;
         if ((e = ensure_smem(k_grid<R, J, MODE>, smem))) return e;
-        k_grid<R, J, MODE><<<ctas, 256, smem, s>>>(src, rb, vv, (const R*)p->blk_scale, act, p->cell,
-                                                  (const R*)p->fx, (const R*)p->fy, p->perm, p->seg_start,
-                                                  p->seg_block, p->tile_seg_start, tiles, count, U, ms, g, toj,
-                                                  beta, p->kbpoly);
+        for (int b = 0; b < batch; ++b)        // kernels wider than 8: one launch per image
+            k_grid<R, J, MODE><<<ctas, 256, smem, s>>>(src ? src + (int64_t)b * p->M : src, rb, vv,
+                                                      (const R*)p->blk_scale, act, p->cell, (const R*)p->fx,
+                                                      (const R*)p->fy, p->perm, p->seg_start, p->seg_block,
+                                                      p->tile_seg_start, tiles, count,
+                                                      U + (int64_t)b * g.Kx * g.Ky, ms, g, toj, beta, p->kbpoly);
     }
     return cudaGetLastError();
 }
@@ -720,16 +773,19 @@ static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const D
 // its tiles from a dynamically claimed position of its list.
 template <typename R>
 static cudaError_t launch_grid(const pd_plan* p, int mode, const cplx_t<R>* src, const DualArgs* a,
-                               const int32_t* const* tiles, const int32_t* counts4, cplx_t<R>* U, cudaStream_t s) {
+                               const int32_t* const* tiles, const int32_t* counts4, cplx_t<R>* U, cudaStream_t s,
+                               int batch = 1) {
     const Geo& g = p->g;
     cudaError_t e = cudaSuccess;
     prof_mark(PH_GRID, 0, s);
     if ((e = cudaMemsetAsync(p->sched, 0, 4 * sizeof(int32_t), s))) return e;
     for (int c = 0; c < 4 && !e; ++c) {
         if (mode == 0) {
-            PD_J_DISPATCH(g.J, (e = launch_grid_j<R, JJ, 0>(p, src, a, tiles[c], counts4 + c, U, p->sched + c, s)));
+            PD_J_DISPATCH(g.J, (e = launch_grid_j<R, JJ, 0>(p, src, a, tiles[c], counts4 + c, U, p->sched + c, s,
+                                                            batch)));
         } else {
-            PD_J_DISPATCH(g.J, (e = launch_grid_j<R, JJ, 1>(p, src, a, tiles[c], counts4 + c, U, p->sched + c, s)));
+            PD_J_DISPATCH(g.J, (e = launch_grid_j<R, JJ, 1>(p, src, a, tiles[c], counts4 + c, U, p->sched + c, s,
+                                                            1)));
         }
     }
     prof_mark(PH_GRID, 1, s);
@@ -737,13 +793,13 @@ static cudaError_t launch_grid(const pd_plan* p, int mode, const cplx_t<R>* src,
 }
 
 template <typename R>
-cudaError_t grid_plain(const pd_plan* p, const cplx_t<R>* y_user, cplx_t<R>* U, cudaStream_t s) {
+cudaError_t grid_plain(const pd_plan* p, const cplx_t<R>* y_user, cplx_t<R>* U, cudaStream_t s, int batch) {
     // U = G^T y: every window is added to a zeroed grid
-    cudaError_t e = cudaMemsetAsync(U, 0, (size_t)p->g.Kx * p->g.Ky * sizeof(cplx_t<R>), s);
+    cudaError_t e = cudaMemsetAsync(U, 0, (size_t)batch * p->g.Kx * p->g.Ky * sizeof(cplx_t<R>), s);
     if (e) return e;
     const int q = p->g.ntiles / 4;
     const int32_t* lists[4] = {p->colour_tiles, p->colour_tiles + q, p->colour_tiles + 2 * q, p->colour_tiles + 3 * q};
-    return launch_grid<R>(p, 0, y_user, nullptr, lists, p->colour_counts, U, s);
+    return launch_grid<R>(p, 0, y_user, nullptr, lists, p->colour_counts, U, s, batch);
 }
 
 template <typename R>
@@ -752,16 +808,16 @@ cudaError_t grid_dual(const pd_plan* p, const DualArgs& a, const int32_t* const*
     return launch_grid<R>(p, 1, nullptr, &a, tiles, counts4, U, s);
 }
 
-template cudaError_t degrid_plain<float>(const pd_plan*, const float2*, float2*, cudaStream_t);
-template cudaError_t degrid_plain<double>(const pd_plan*, const double2*, double2*, cudaStream_t);
+template cudaError_t degrid_plain<float>(const pd_plan*, const float2*, float2*, cudaStream_t, int);
+template cudaError_t degrid_plain<double>(const pd_plan*, const double2*, double2*, cudaStream_t, int);
 template cudaError_t degrid_res_norms<float>(const pd_plan*, const float2*, const float2*, double*, cudaStream_t);
 template cudaError_t degrid_res_norms<double>(const pd_plan*, const double2*, const double2*, double*, cudaStream_t);
 template cudaError_t degrid_dual<float>(const pd_plan*, const float2*, const DualArgs&, const int32_t*,
                                         const int32_t*, cudaStream_t);
 template cudaError_t degrid_dual<double>(const pd_plan*, const double2*, const DualArgs&, const int32_t*,
                                          const int32_t*, cudaStream_t);
-template cudaError_t grid_plain<float>(const pd_plan*, const float2*, float2*, cudaStream_t);
-template cudaError_t grid_plain<double>(const pd_plan*, const double2*, double2*, cudaStream_t);
+template cudaError_t grid_plain<float>(const pd_plan*, const float2*, float2*, cudaStream_t, int);
+template cudaError_t grid_plain<double>(const pd_plan*, const double2*, double2*, cudaStream_t, int);
 template cudaError_t grid_dual<float>(const pd_plan*, const DualArgs&, const int32_t* const*, const int32_t*,
                                       float2*, cudaStream_t);
 template cudaError_t grid_dual<double>(const pd_plan*, const DualArgs&, const int32_t* const*, const int32_t*,

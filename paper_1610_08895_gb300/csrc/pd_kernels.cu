@@ -122,44 +122,57 @@ __global__ void __launch_bounds__(SEL_NT) k_select(
     for (int i = tid; i < d; i += SEL_NT) block_active[i] = philox_uniform(seed, (uint64_t)t, 0, i) < p_block[i];
     for (int j = tid; j < b; j += SEL_NT) basis_active[j] = philox_uniform(seed, (uint64_t)t, 1, j) < p_basis[j];
     __syncthreads();
-    // active tiles, in the static heaviest-first order; count active segments too
+    // active tiles, in the static heaviest-first order (all of them for the degridding,
+    // and split by colour for the gridding); count active segments too
     {
         const int per = (ntiles + SEL_NT - 1) / SEL_NT;
         const int k0 = min(ntiles, tid * per), k1 = min(ntiles, k0 + per);
-        int mine = 0, segs = 0;
+        int mine = 0, segs = 0, mc[4] = {0, 0, 0, 0};
+        // batches of tiles whose independent loads go out together
+        constexpr int TB = 8;
+        for (int kb = k0; kb < k1; kb += TB) {
+            int tt[TB], s0[TB], s1[TB];
+#pragma unroll
+            for (int i = 0; i < TB; ++i) tt[i] = kb + i < k1 ? tile_order[kb + i] : -1;
+#pragma unroll
+            for (int i = 0; i < TB; ++i) {
+                s0[i] = tt[i] >= 0 ? tile_seg_start[tt[i]] : 0;
+                s1[i] = tt[i] >= 0 ? tile_seg_start[tt[i] + 1] : 0;
+            }
+#pragma unroll
+            for (int i = 0; i < TB; ++i) {
+                if (tt[i] < 0) continue;
+                int on = 0;
+                for (int sg = s0[i]; sg < s1[i]; ++sg) {
+                    const int a = block_active[seg_block[sg]];
+                    on |= a;
+                    segs += a;
+                }
+                tile_active[tt[i]] = on;
+                mine += on;
+                if (on) mc[tile_colour(tt[i], ntx)]++;
+            }
+        }
+        int excl, sexcl, cex[4];
+        const int total = block_excl_scan(mine, shi, excl);
+        const int stotal = block_excl_scan(segs, shi, sexcl);
+        int ctot[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ctot[c] = block_excl_scan(mc[c], shi, cex[c]);
+        const int q = ntiles / 4;
         for (int k = k0; k < k1; ++k) {
             const int tt = tile_order[k];
-            int on = 0;
-            for (int sg = tile_seg_start[tt]; sg < tile_seg_start[tt + 1]; ++sg) {
-                const int a = block_active[seg_block[sg]];
-                on |= a;
-                segs += a;
+            if (tile_active[tt]) {
+                act_tiles[excl++] = tt;
+                const int c = tile_colour(tt, ntx);
+                act_col[c * q + cex[c]++] = tt;
             }
-            tile_active[tt] = on;
-            mine += on;
         }
-        int excl;
-        const int total = block_excl_scan(mine, shi, excl);
-        int mc[4] = {0, 0, 0, 0};
-        for (int k = k0; k < k1; ++k)
-            if (tile_active[tile_order[k]]) {
-                act_tiles[excl++] = tile_order[k];
-                mc[tile_colour(tile_order[k], ntx)]++;
-            }
-        int sexcl;
-        const int stotal = block_excl_scan(segs, shi, sexcl);
-        if (tid == 0) { counts[0] = stotal; counts[1] = total; }
-        // the same tiles split by colour (each colour keeps the heaviest-first order)
-        const int q = ntiles / 4;
+        if (tid == 0) {
+            counts[0] = stotal;
+            counts[1] = total;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            int cex;
-            const int ctot = block_excl_scan(mc[c], shi, cex);
-            for (int k = k0; k < k1; ++k) {
-                const int tt = tile_order[k];
-                if (tile_active[tt] && tile_colour(tt, ntx) == c) act_col[c * q + cex++] = tt;
-            }
-            if (tid == 0) counts[2 + c] = ctot;
+            for (int c = 0; c < 4; ++c) counts[2 + c] = ctot[c];
         }
     }
 }

@@ -102,6 +102,10 @@ struct pd_plan {
     void* t1 = nullptr;            // complex [nx/PW + 1][ny][PW] half-spectrum row-pass intermediate
     void* gridb = nullptr;         // complex [nx/PW + 1][Ky][PW] b~ = F Z x~, columns 0 .. nx
     void* gridu = nullptr;         // complex grid for the plain adjoint
+    int batch_cap = 0;             // images the batch scratch below holds (0: none yet)
+    void* bt1 = nullptr;           // batch scratch of pd_apply_phi / pd_apply_phi_adj: t1, F Z x, U
+    void* bgb = nullptr;
+    void* bgu = nullptr;
     void* rbuf = nullptr;          // complex [M] residuals r = v + G b - y (internal order)
     double* seg_part = nullptr;    // [2 * nseg] per-segment FP64 partial norms
     double* blk_norm = nullptr;    // [2 * d]: ||r_i||^2, ||G_i b - y_i||^2
@@ -181,8 +185,11 @@ void prof_mark(int phase, int end, cudaStream_t s);
 pd_status set_error(pd_status st, const char* msg);
 
 // ---- fft.cu
+// batch images at once (blockIdx.y); t1: the half-spectrum intermediate of the batch
+// (nullptr = the plan's own, for batch 1)
 template <typename R>
-cudaError_t fwd_fft(const pd_plan* p, const R* x, cplx_t<R>* grid, cudaStream_t s);
+cudaError_t fwd_fft(const pd_plan* p, const R* x, cplx_t<R>* grid, cudaStream_t s, int batch = 1,
+                    cplx_t<R>* t1 = nullptr);
 struct PrimalArgs {
     double tau, sigma, varsigma;
     void* x;           // in/out
@@ -192,7 +199,8 @@ struct PrimalArgs {
 };
 // mode 0: write Re(Z^T F^H grid) to out; mode 1: primal update (Alg. 1 steps 17-18)
 template <typename R>
-cudaError_t inv_fft(const pd_plan* p, const cplx_t<R>* grid, R* out, const PrimalArgs* pa, cudaStream_t s);
+cudaError_t inv_fft(const pd_plan* p, const cplx_t<R>* grid, R* out, const PrimalArgs* pa, cudaStream_t s,
+                    int batch = 1, cplx_t<R>* t1 = nullptr);
 int inv_rows_ctas(const pd_plan* p);
 
 // ---- gridding.cu
@@ -203,9 +211,9 @@ struct DualArgs {
     const double* eps;
     double* res_norm;     // updated for active blocks
 };
-// plain degrid: out (user order) = G grid
+// plain degrid of `batch` half grids (stride: one image's half grid) into out (user order, stride M)
 template <typename R>
-cudaError_t degrid_plain(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out_user, cudaStream_t s);
+cudaError_t degrid_plain(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out_user, cudaStream_t s, int batch = 1);
 // ||G_i grid - y_i|| of every block into res_norm (the exact reading of Sec. 4's c_i)
 template <typename R>
 cudaError_t degrid_res_norms(const pd_plan* p, const cplx_t<R>* grid, const cplx_t<R>* y, double* res_norm,
@@ -214,9 +222,9 @@ cudaError_t degrid_res_norms(const pd_plan* p, const cplx_t<R>* grid, const cplx
 template <typename R>
 cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs& a, const int32_t* tiles,
                         const int32_t* counts, cudaStream_t s);
-// plain grid: U = G^T y_user (U overwritten)
+// plain grid: U = G^T y_user (U overwritten) for `batch` inputs (stride M) and grids (stride Kx Ky)
 template <typename R>
-cudaError_t grid_plain(const pd_plan* p, const cplx_t<R>* y_user, cplx_t<R>* U, cudaStream_t s);
+cudaError_t grid_plain(const pd_plan* p, const cplx_t<R>* y_user, cplx_t<R>* U, cudaStream_t s, int batch = 1);
 // pd grid over the listed tiles, one launch per colour (tiles[c]: device list of colour c,
 // counts4[c]: device count): v <- scale * r, U += G^T (v_new - v_old)
 template <typename R>

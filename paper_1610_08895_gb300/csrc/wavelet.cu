@@ -56,10 +56,13 @@ __device__ __forceinline__ void load_filters(const R* __restrict__ filt, int k, 
 constexpr int ARB = 4;   // analysis outputs per thread along a row (row pass) or column (column pass)
 
 // One analysis level of basis k on an output tile of ty x tx per sub-band at (oy0, ox0)
-// of the (my x mx) region. Staged input rows have pitch IWP (a multiple of 4). Row pass:
-// a thread computes ARB consecutive outputs of one input row from LF + 2 ARB - 2 staged
-// values; column pass: ARB consecutive output rows of one column. MODE 0 writes the
-// scaled coefficients, MODE 1 the step-13 update of s and its change ds.
+// of the (my x mx) region. Staged input rows have an odd pitch IWP and the row-pass
+// results a pitch tx + 1, so that threads walking down a column hit distinct banks.
+// Row pass: a thread computes ARB consecutive outputs of one input row from
+// LF + 2 ARB - 2 staged values (consecutive threads take consecutive rows); column
+// pass: ARB consecutive output rows of one column, the low-pass half (LL, LH) and then
+// the high-pass half (HL, HH). MODE 0 writes the scaled coefficients, MODE 1 the
+// step-13 update of s and its change ds.
 template <typename R, int MODE, int LF>
 __device__ __forceinline__ void dwt_body(const R* __restrict__ src, R* __restrict__ ll_out, R* __restrict__ out,
                                          R* __restrict__ ds, const R* __restrict__ filt, int k, int my, int mx,
@@ -67,31 +70,12 @@ __device__ __forceinline__ void dwt_body(const R* __restrict__ src, R* __restric
                                          int64_t ll_off, R scale, R alpha, R* sm) {
     constexpr int NX = LF + 2 * ARB - 2;               // staged values per ARB outputs
     const int hy = my >> 1, hx = mx >> 1;
-    const int IH = 2 * ty + LF - 2, IW = 2 * tx + LF - 2, IWP = (IW + 3) & ~3;
+    const int IH = 2 * ty + LF - 2, IW = 2 * tx + LF - 2, IWP = IW | 1, TP = tx + 1;
     R* in = sm;                                        // [IH][IWP]
-    R* ra = in + IH * IWP;                             // [IH][tx]
-    R* rd = ra + IH * tx;                              // [IH][tx]
+    R* ra = in + IH * IWP;                             // [IH][TP]
+    R* rd = ra + IH * TP;                              // [IH][TP]
     R h[LF], g[LF];
     load_filters<R, LF>(filt, k, h, g);
-    // column-pass work item of this thread: rows r0 .. r0 + ARB - 1 of column c
-    const int ncg = (ty + ARB - 1) / ARB;
-    const int item = threadIdx.x;
-    const bool colwork = item < ncg * tx;
-    const int c = colwork ? item % tx : 0, r0 = colwork ? (item / tx) * ARB : 0;
-    // step 13 reads the current s of this thread's outputs: issue those loads first
-    R s_old[ARB][4];
-    if (MODE == 1 && colwork) {
-#pragma unroll
-        for (int i = 0; i < ARB; ++i) {
-            if (r0 + i < ty) {
-                const int oy = oy0 + r0 + i, ox = ox0 + c;
-                s_old[i][0] = out[boff + (int64_t)oy * nx + hx + ox];
-                s_old[i][1] = out[boff + (int64_t)(hy + oy) * nx + ox];
-                s_old[i][2] = out[boff + (int64_t)(hy + oy) * nx + hx + ox];
-                s_old[i][3] = last ? out[boff + (int64_t)oy * nx + ox] : R(0);
-            }
-        }
-    }
     stage_batched<8>(in, IH * IWP, [&](int i) {
         const int r = i / IWP, cc = i - r * IWP;
         const int gy = (2 * oy0 + r) & (my - 1), gx = (2 * ox0 + cc) & (mx - 1);
@@ -101,7 +85,7 @@ __device__ __forceinline__ void dwt_body(const R* __restrict__ src, R* __restric
     // row pass
     const int nrg = (tx + ARB - 1) / ARB;
     for (int it = threadIdx.x; it < IH * nrg; it += blockDim.x) {
-        const int r = it / nrg, c0 = (it - r * nrg) * ARB;
+        const int r = it % IH, c0 = (it / IH) * ARB;
         const R* row = in + r * IWP + 2 * c0;
         R x[NX];
 #pragma unroll
@@ -111,51 +95,66 @@ __device__ __forceinline__ void dwt_body(const R* __restrict__ src, R* __restric
             R a = 0, d = 0;
 #pragma unroll
             for (int j = 0; j < LF; ++j) { a += h[j] * x[2 * o + j]; d += g[j] * x[2 * o + j]; }
-            if (c0 + o < tx) { ra[r * tx + c0 + o] = a; rd[r * tx + c0 + o] = d; }
+            if (c0 + o < tx) { ra[r * TP + c0 + o] = a; rd[r * TP + c0 + o] = d; }
         }
     }
     __syncthreads();
-    if (!colwork) return;
-    R va[NX], vd[NX];
+    // column pass: rows r0 .. r0 + ARB - 1 of column c
+    const int ncg = (ty + ARB - 1) / ARB;
+    for (int item = threadIdx.x; item < ncg * tx; item += blockDim.x) {
+        const int c = item % tx, r0 = (item / tx) * ARB;
+        const int ox = ox0 + c;
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            // half 0: the low-pass rows (LL, LH); half 1: the high-pass rows (HL, HH)
+            const R* rr = half ? rd : ra;
+            R sold[ARB][2];
+            if (MODE == 1) {
 #pragma unroll
-    for (int i = 0; i < NX; ++i) {
-        const int rr = 2 * r0 + i;
-        va[i] = rr < IH ? ra[rr * tx + c] : R(0);
-        vd[i] = rr < IH ? rd[rr * tx + c] : R(0);
-    }
+                for (int o = 0; o < ARB; ++o) {
+                    const int oy = oy0 + r0 + o;
+                    if (r0 + o < ty) {
+                        sold[o][0] = half ? out[boff + (int64_t)oy * nx + hx + ox]
+                                          : (last ? out[boff + (int64_t)oy * nx + ox] : R(0));
+                        sold[o][1] = out[boff + (int64_t)(hy + oy) * nx + (half ? hx : 0) + ox];
+                    }
+                }
+            }
+            R v[NX];
 #pragma unroll
-    for (int o = 0; o < ARB; ++o) {
-        if (r0 + o >= ty) break;
-        R ll = 0, hl = 0, lh = 0, hh = 0;
+            for (int i = 0; i < NX; ++i) v[i] = 2 * r0 + i < IH ? rr[(2 * r0 + i) * TP + c] : R(0);
 #pragma unroll
-        for (int j = 0; j < LF; ++j) {
-            const R a = va[2 * o + j], d = vd[2 * o + j];
-            ll += h[j] * a; lh += g[j] * a;
-            hl += h[j] * d; hh += g[j] * d;
+            for (int o = 0; o < ARB; ++o) {
+                if (r0 + o >= ty) break;
+                R lo = 0, hi = 0;
+#pragma unroll
+                for (int j = 0; j < LF; ++j) { lo += h[j] * v[2 * o + j]; hi += g[j] * v[2 * o + j]; }
+                const int oy = oy0 + r0 + o;
+                // low-pass along y: LL (half 0) or HL (half 1); high-pass along y: LH or HH
+                const int64_t p_lo = boff + (int64_t)oy * nx + (half ? hx : 0) + ox;
+                const int64_t p_hi = boff + (int64_t)(hy + oy) * nx + (half ? hx : 0) + ox;
+                const bool store_lo = half || last;
+                if (MODE == 0) {
+                    if (store_lo) out[p_lo] = lo * scale;
+                    out[p_hi] = hi * scale;
+                } else {
+                    if (store_lo) {
+                        const R so = sold[o][0], sn = clip(so + lo * scale, alpha);
+                        out[p_lo] = sn; ds[p_lo] = sn - so;
+                    }
+                    const R so = sold[o][1], sn = clip(so + hi * scale, alpha);
+                    out[p_hi] = sn; ds[p_hi] = sn - so;
+                }
+                if (!half && !last) ll_out[ll_off + (int64_t)oy * hx + ox] = lo;
+            }
         }
-        const int oy = oy0 + r0 + o, ox = ox0 + c;
-        const int64_t p_hl = boff + (int64_t)oy * nx + hx + ox;
-        const int64_t p_lh = boff + (int64_t)(hy + oy) * nx + ox;
-        const int64_t p_hh = boff + (int64_t)(hy + oy) * nx + hx + ox;
-        const int64_t p_ll = boff + (int64_t)oy * nx + ox;
-        if (MODE == 0) {
-            out[p_hl] = hl * scale; out[p_lh] = lh * scale; out[p_hh] = hh * scale;
-            if (last) out[p_ll] = ll * scale;
-        } else {
-            R so, sn;
-            so = s_old[o][0]; sn = clip(so + hl * scale, alpha); out[p_hl] = sn; ds[p_hl] = sn - so;
-            so = s_old[o][1]; sn = clip(so + lh * scale, alpha); out[p_lh] = sn; ds[p_lh] = sn - so;
-            so = s_old[o][2]; sn = clip(so + hh * scale, alpha); out[p_hh] = sn; ds[p_hh] = sn - so;
-            if (last) { so = s_old[o][3]; sn = clip(so + ll * scale, alpha); out[p_ll] = sn; ds[p_ll] = sn - so; }
-        }
-        if (!last) ll_out[ll_off + (int64_t)oy * hx + ox] = ll;
     }
 }
 
 // One level for every basis in blockIdx.z. MODE 0: out = coefficient * scale.
 // MODE 1: s/ds update of step 13. The last level also treats the approximation band.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(NT_W) k_dwt_level(const R* __restrict__ x0, const R* __restrict__ ll_in,
+__global__ void __launch_bounds__(NT_W, 3) k_dwt_level(const R* __restrict__ x0, const R* __restrict__ ll_in,
                                                     R* __restrict__ ll_out, R* __restrict__ out, R* __restrict__ ds,
                                                     const R* __restrict__ filt, const int32_t* __restrict__ flen,
                                                     const int32_t* __restrict__ active, int level, int L, int ny,
@@ -204,7 +203,7 @@ constexpr int SRP = 2;   // synthesis: output row pairs per thread (column pass)
 
 // Reconstruct a (ty x tx) tile of the level-`level` region (size my x mx) of basis k from
 // its four sub-bands; the approximation band comes from ll_in (or from the packed
-// coefficients at the coarsest level). Result left in `res` (shared, [ty][tx]).
+// coefficients at the coarsest level). Result left in `res` (shared, [ty][tx + 1]).
 // Output rows 2m and 2m + 1 both read the sub-band rows m + off - i, i < LF/2 (even and
 // odd taps): a thread computes SRP row pairs of one column from LF/2 + SRP - 1 staged
 // values per band; the row pass likewise along the rows.
@@ -221,8 +220,9 @@ __device__ __forceinline__ void synth_tile(const R* __restrict__ coef, const R* 
     R* HLs = LLs + NKy * NKx;
     R* LHs = HLs + NKy * NKx;
     R* HHs = LHs + NKy * NKx;
-    R* lo = HHs + NKy * NKx;          // [ty][NKx] columns synthesised, low-x half
-    R* hi = lo + ty * NKx;
+    const int NKP = NKx | 1;          // odd pitch: threads walking down a column hit distinct banks
+    R* lo = HHs + NKy * NKx;          // [ty][NKP] columns synthesised, low-x half
+    R* hi = lo + ty * NKP;
     R h[LF], g[LF];
     load_filters<R, LF>(filt, k, h, g);
     const int64_t boff = (int64_t)k * ny * nx;
@@ -278,22 +278,22 @@ __device__ __forceinline__ void synth_tile(const R* __restrict__ coef, const R* 
                     l += h[j] * a[0][q] + g[j] * a[1][q];
                     hh += h[j] * a[2][q] + g[j] * a[3][q];
                 }
-                lo[(2 * m + par) * NKx + c] = l;
-                hi[(2 * m + par) * NKx + c] = hh;
+                lo[(2 * m + par) * NKP + c] = l;
+                hi[(2 * m + par) * NKP + c] = hh;
             }
         }
     }
     __syncthreads();
-    // row pass: columns 2m .. 2m + 2 SRP - 1 of row r
+    // row pass: columns 2m .. 2m + 2 SRP - 1 of row r (consecutive threads take consecutive rows)
     const int npc = (tx / 2 + SRP - 1) / SRP;
     for (int it = threadIdx.x; it < ty * npc; it += blockDim.x) {
-        const int r = it / npc, m0 = (it - r * npc) * SRP;
+        const int r = it % ty, m0 = (it / ty) * SRP;
         R bl[NV], bh[NV];
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
             const int kk = m0 + i;
-            bl[i] = kk < NKx ? lo[r * NKx + kk] : R(0);
-            bh[i] = kk < NKx ? hi[r * NKx + kk] : R(0);
+            bl[i] = kk < NKx ? lo[r * NKP + kk] : R(0);
+            bh[i] = kk < NKx ? hi[r * NKP + kk] : R(0);
         }
 #pragma unroll
         for (int pq = 0; pq < SRP; ++pq) {
@@ -307,7 +307,7 @@ __device__ __forceinline__ void synth_tile(const R* __restrict__ coef, const R* 
                     const int j = 2 * i + par, q = pq + LF / 2 - 1 - i;
                     v += h[j] * bl[q] + g[j] * bh[q];
                 }
-                res[r * tx + 2 * m + par] = v;
+                res[r * (tx + 1) + 2 * m + par] = v;
             }
         }
     }
@@ -333,12 +333,12 @@ __global__ void __launch_bounds__(NT_W) k_idwt_level(const R* __restrict__ coef,
     const int oy0 = blockIdx.y * ty, ox0 = blockIdx.x * tx;
     if (oy0 >= my || ox0 >= mx) return;
     R* sm = reinterpret_cast<R*>(smraw);
-    R* res = sm + 4 * (ty / 2 + MAX_FILTER / 2) * (tx / 2 + MAX_FILTER / 2) + 2 * ty * (tx / 2 + MAX_FILTER / 2);
+    R* res = sm + 4 * (ty / 2 + MAX_FILTER / 2) * (tx / 2 + MAX_FILTER / 2) + 2 * ty * ((tx / 2 + MAX_FILTER / 2) | 1);
     PD_LF_DISPATCH(lf, (synth_tile<R, LF>(coef, ll_in, filt, k, level, L, ny, nx, oy0, ox0, ty, tx, sm, res)));
     R* dst = ll_out + (int64_t)k * out_stride;
     for (int i = threadIdx.x; i < ty * tx; i += blockDim.x) {
         const int r = i / tx, c = i - r * tx;
-        dst[(int64_t)(oy0 + r) * mx + ox0 + c] = res[i];
+        dst[(int64_t)(oy0 + r) * mx + ox0 + c] = res[r * (tx + 1) + c];
     }
 }
 
@@ -387,12 +387,12 @@ __global__ void __launch_bounds__(256) k_syn_sum(const R* __restrict__ coef, con
 
 // -------------------------------------------------------------------- launchers
 template <typename R> static size_t ana_smem(int ty, int tx) {
-    const int IH = 2 * ty + MAX_FILTER - 2, IWP = (2 * tx + MAX_FILTER - 2 + 3) & ~3;
-    return (size_t)(IH * IWP + 2 * IH * tx) * sizeof(R);
+    const int IH = 2 * ty + MAX_FILTER - 2, IWP = (2 * tx + MAX_FILTER - 2) | 1;
+    return (size_t)(IH * IWP + 2 * IH * (tx + 1)) * sizeof(R);
 }
 template <typename R> static size_t syn_smem(int ty, int tx) {
     const int NKy = ty / 2 + MAX_FILTER / 2, NKx = tx / 2 + MAX_FILTER / 2;
-    return (size_t)(4 * NKy * NKx + 2 * ty * NKx + ty * tx) * sizeof(R);
+    return (size_t)(4 * NKy * NKx + 2 * ty * (NKx | 1) + ty * (tx + 1)) * sizeof(R);
 }
 
 template <typename R>

@@ -13,6 +13,10 @@ Sec. 5 of arXiv:1610.08895, which are not available here):
   edge is pi), points outside [-pi, pi)^2 redrawn.
 * uv "radial": area density proportional to 8^(-r/pi) for r < pi (the inner
   density is 8x the outer), uniform angle.
+* uv "gaussian with holes": the Gaussian coverage with circular holes cut mostly in
+  the high frequencies (Sec. 5: holes placed with an inverse Gaussian profile): hole
+  centres are drawn with density proportional to 1 - exp(-r^2 / (2 s^2)) (low at the
+  origin, high towards the band edge), and points falling in a hole are redrawn.
 * blocks "equal": sqrt(d) equal-count strips in u, each cut into sqrt(d)
   equal-count pieces in v (compact uv regions, Sec. 3).
 * blocks "annuli": equal-width radial annuli over [0, pi); "annuli_sectors"
@@ -59,6 +63,35 @@ def uv_gaussian(m, seed=0, sd=0.25 * np.pi):
         ok = np.all((cand >= -np.pi) & (cand < np.pi), axis=1)
         out = np.concatenate([out, cand[ok]])
     return out[:m].copy()
+
+
+def uv_gaussian_holes(m, seed=0, sd=0.25 * np.pi, nholes=40, hole_radius=(0.05 * np.pi, 0.15 * np.pi),
+                      profile_sd=0.5 * np.pi):
+    """m points of the clipped 2-D Gaussian coverage with nholes circular holes; returns
+    (uv [m, 2], holes [nholes, 3] as (centre u, centre v, radius))."""
+    rng = _rng(seed)
+    centres = np.empty((0, 2))
+    while len(centres) < nholes:
+        c = rng.uniform(-np.pi, np.pi, size=(4 * nholes, 2))
+        keep = rng.uniform(0.0, 1.0, len(c)) < 1.0 - np.exp(-np.sum(c * c, axis=1) / (2.0 * profile_sd ** 2))
+        centres = np.concatenate([centres, c[keep]])
+    centres = centres[:nholes]
+    radii = rng.uniform(hole_radius[0], hole_radius[1], nholes)
+    holes = np.column_stack([centres, radii])
+
+    def outside(p):
+        d2 = (p[:, None, 0] - centres[None, :, 0]) ** 2 + (p[:, None, 1] - centres[None, :, 1]) ** 2
+        return np.all(d2 >= radii[None, :] ** 2, axis=1)
+    out = np.empty((0, 2))
+    while len(out) < m:
+        cand = rng.normal(0.0, sd, size=(2 * (m - len(out)) + 16, 2))
+        ok = np.all((cand >= -np.pi) & (cand < np.pi), axis=1)
+        cand = cand[ok]
+        keep = np.zeros(len(cand), dtype=bool)
+        for a in range(0, len(cand), 1 << 16):
+            keep[a:a + (1 << 16)] = outside(cand[a:a + (1 << 16)])
+        out = np.concatenate([out, cand[keep]])
+    return out[:m].copy(), holes
 
 
 def uv_radial(m, seed=0, contrast=8.0):

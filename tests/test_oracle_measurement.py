@@ -167,3 +167,17 @@ def test_adjoint_at_pixels_equals_full_adjoint():
     pix = [(0, 0), (7, 31), (15, 3), (8, 16), (3, 29)]
     got = geo.phi_adj_at(y, uv, pix)
     assert np.allclose(got, [full[iy, ix] for iy, ix in pix], rtol=1e-11, atol=1e-11 * np.abs(full).max())
+
+
+def test_uv_coverage_with_holes():
+    # Sec. 5: holes cut predominantly in the high frequencies (inverse Gaussian profile)
+    from paper_1610_08895_gb300 import synth
+    uv, holes = synth.uv_gaussian_holes(20000, seed=3, nholes=40)
+    assert uv.shape == (20000, 2) and np.all((uv >= -np.pi) & (uv < np.pi))
+    d2 = (uv[:, None, 0] - holes[None, :, 0]) ** 2 + (uv[:, None, 1] - holes[None, :, 1]) ** 2
+    assert np.all(d2 >= holes[None, :, 2] ** 2)                      # no point inside a hole
+    r = np.hypot(holes[:, 0], holes[:, 1])
+    r_unif = np.hypot(*np.random.default_rng(0).uniform(-np.pi, np.pi, (100000, 2)).T)
+    assert np.mean(r) > np.mean(r_unif)                             # centres lean to high frequencies
+    uv2, holes2 = synth.uv_gaussian_holes(20000, seed=3, nholes=40)
+    assert np.array_equal(uv, uv2) and np.array_equal(holes, holes2)
