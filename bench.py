@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-operators", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0, help="gridding tile edge (0: the plan's default)")
+    ap.add_argument("--profile-run", type=int, default=0,
+                    help="profiling target: plan the workload, set data and start values, run this many eager "
+                         "iterations with fixed step sizes (no power method, no timing) and exit")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip pd_plan_autotune (16, 32, 64) and plan with --tile (0: the plan's default)")
     ap.add_argument("--cpu-full", type=int, default=0,
@@ -458,6 +461,32 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------------------------
+def run_profile_target(args):
+    """A short, deterministic launch sequence for ncu: plan, y from synthetic noise, start
+    values x^(0) = x~^(0) = the test image, then args.profile_run eager iterations (per
+    iteration: draws, 4 analysis + 4 synthesis levels and the sum, 2 forward passes,
+    degridding, block norms, 4 gridding colour launches, 2 inverse passes, primal sums)."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1610_08895_gb300.api import Plan, State
+    cfg = WORKLOADS[args.workload]
+    n, m = cfg["n"], cfg["m"]
+    uv, blk, x_true, noise = make_inputs(cfg, args.seed)
+    d = int(blk.max()) + 1
+    b = len(cfg["bases"])
+    plan = Plan(n, n, uv, blk, d, kernel_width=cfg["J"], basis_ids=cfg["bases"], levels=cfg["levels"],
+                precision="f32", tile=args.tile)
+    st = State(plan)
+    st.pd_state_set_data(torch.tensor(10.0 * noise, dtype=torch.complex64, device="cuda"), np.full(d, 30.0))
+    x0 = torch.tensor(x_true, dtype=torch.float32, device="cuda")
+    st.pd_state_set_start(x0, x0)
+    st.pd_iterate(args.profile_run, tau=0.49, sigma=1.0, varsigma=1e-7, kappa=1e-3, psi_norm=1.0, seed=args.seed,
+                  p_block=[cfg["p"]] * d, p_basis=[cfg["p"]] * b)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": args.profile_run, "workload": args.workload, "plan": plan.info()}))
+
+
 def oracle_problem(cfg, seed):
     """The oracle's problem on a workload (used only by the CPU legs)."""
     from oracle import experiment as EX
@@ -598,7 +627,9 @@ def run_cpu_full(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.cpu_full:
+    if a.profile_run:
+        run_profile_target(a)
+    elif a.cpu_full:
         run_cpu_full(a)
     elif a.impl == "reference":
         run_reference(a)

@@ -236,6 +236,8 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
             const int ly = by[m] & (g.tile - 1), lx = bx[m] & (g.tile - 1);
             return (ly / SC) * p->nsc_side + lx / SC;
         };
+        const int nsc = p->nsc_side * p->nsc_side;
+        std::vector<int32_t> sc_start((size_t)p->nseg * (nsc + 1));
         for (int64_t sg = 0; sg < p->nseg; ++sg) {
             std::stable_sort(order.begin() + seg_start[sg], order.begin() + seg_start[sg + 1],
                              [&](int32_t a, int32_t b2) {
@@ -243,7 +245,15 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
                                  if (sa != sb) return sa < sb;
                                  return (by[a] != by[b2]) ? by[a] < by[b2] : bx[a] < bx[b2];
                              });
+            // start of each super-cell's points inside the segment (the gridding's per-warp ranges)
+            int32_t* o = &sc_start[(size_t)sg * (nsc + 1)];
+            int i = seg_start[sg];
+            for (int k = 0; k <= nsc; ++k) {
+                while (i < seg_start[sg + 1] && scell_of(order[i]) < k) ++i;
+                o[k] = i;
+            }
         }
+        p->h_sc_start = std::move(sc_start);
         // segments of each block (tile order) for the fixed-order block reductions
         std::vector<int32_t> bss(p->d + 1, 0), bsl(p->nseg);
         for (int64_t sg = 0; sg < p->nseg; ++sg) bss[seg_block[sg] + 1]++;
@@ -273,6 +283,10 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         ALLOC(p->block_seg_start, bss.size());
         ALLOC(p->block_seg_list, bsl.size());
         ALLOC(p->tile_order, tord.size());
+        ALLOC(p->seg_sc_start, p->h_sc_start.size());
+        CU(upload(p->seg_sc_start, p->h_sc_start));
+        p->h_sc_start.clear();
+        p->h_sc_start.shrink_to_fit();
         {
             // tiles of each colour in heaviest-first order
             const int q = g.ntiles / 4;

@@ -161,26 +161,11 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
         const int seg0 = tile_seg_start[t], nseg_t = tile_seg_start[t + 1] - seg0;
         list_active_segments(seg0, nseg_t, seg_block, MODE == 1 ? active : nullptr, seg_start, act_seg, act_pre,
                              &nact_s);
-        // the window, four cells' loads in flight per thread
-        for (int i0 = threadIdx.x; i0 < E * E; i0 += 4 * (int)blockDim.x) {
-            C2 gv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * (int)blockDim.x;
-                if (i < E * E) {
-                    const int ey = i / E, ex = i - ey * E;
-                    gv[u] = half_grid_at(gimg, (oy - H + ey) & (g.Ky - 1), (ox - H + ex) & (g.Kx - 1), g);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * (int)blockDim.x;
-                if (i < E * E) {
-                    const int ey = i / E, ex = i - ey * E;
-                    win[ey * EP + ex] = gv[u];
-                    if (PAIRS && ex > 0) win[E * EP + ey * EP + ex - 1] = gv[u];
-                }
-            }
+        for (int i = threadIdx.x; i < E * E; i += blockDim.x) {
+            const int ey = i / E, ex = i - ey * E;
+            const C2 gv = half_grid_at(gimg, (oy - H + ey) & (g.Ky - 1), (ox - H + ex) & (g.Kx - 1), g);
+            win[ey * EP + ex] = gv;
+            if (PAIRS && ex > 0) win[E * EP + ey * EP + ex - 1] = gv;
         }
         if (MODE == 1)
             for (int i = threadIdx.x; i < 16 * nseg_t; i += blockDim.x) part[i] = 0.0;
@@ -188,33 +173,17 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
         const int nact = nact_s, total = act_pre[nact];
         double* mypart = part + 2 * nseg_t * warp;
         int j = 0;   // segment cursor: positions only grow, so it only moves forward
-        // the inputs of a thread's next point are loaded while the current one is computed
-        struct Pt { int m, js, c; R fx, fy; C2 yy, vv; };
-        auto load_pt = [&](int pos) {
-            Pt q;
-            while (act_pre[j + 1] <= pos) ++j;
-            q.js = j;
-            q.m = seg_start[act_seg[j]] + pos - act_pre[j];
-            q.fx = fxs[q.m];
-            q.fy = fys[q.m];
-            q.c = cell[q.m];
-            if (MODE == 1) { q.yy = y[q.m]; q.vv = v[q.m]; }
-            return q;
-        };
-        Pt cur{};
-        if ((int)threadIdx.x < total) cur = load_pt(threadIdx.x);
         for (int base = 0; base < total; base += blockDim.x) {
             const int pos = base + threadIdx.x;
             const bool ok = pos < total;
-            Pt nxt{};
-            if (pos + (int)blockDim.x < total) nxt = load_pt(pos + blockDim.x);
             R ar = R(0), ad = R(0);     // squares in the working precision (exact for FP64)
             if (ok) {
-                const int m = cur.m;
+                while (act_pre[j + 1] <= pos) ++j;
+                const int m = seg_start[act_seg[j]] + pos - act_pre[j];
                 R wx[J], wy[J];
-                kb_taps<R, J>(cur.fx, wx, two_over_j, beta, kp);
-                kb_taps<R, J>(cur.fy, wy, two_over_j, beta, kp);
-                const int c = cur.c;
+                kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
+                kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
+                const int c = cell[m];
                 const int r0 = (c >> 16) - oy, c0 = (c & 0xFFFF) - ox;   // footprint origin in the window
                 R sx = 0, sy = 0;
                 if constexpr (PAIRS) {
@@ -250,16 +219,15 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                 if (MODE == 0) {
                     oimg[perm[m]] = mk<C2>(sx, sy);
                 } else {
-                    const R dx = sx - cur.yy.x, dy = sy - cur.yy.y;
-                    const C2 r = mk<C2>(cur.vv.x + dx, cur.vv.y + dy);
+                    const C2 yy = y[m], vv = v[m];
+                    const R dx = sx - yy.x, dy = sy - yy.y;
+                    const C2 r = mk<C2>(vv.x + dx, vv.y + dy);
                     rbuf[m] = r;
                     ar = r.x * r.x + r.y * r.y;
                     ad = dx * dx + dy * dy;
                 }
             }
-            const int jcur = cur.js;
-            cur = nxt;
-            if (MODE == 1) warp_seg_add(ok, jcur, ar, ad, mypart);
+            if (MODE == 1) warp_seg_add(ok, j, ar, ad, mypart);
         }
         __syncthreads();
         if (MODE == 1) {
@@ -411,24 +379,26 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
     }
 }
 
-// J <= 8 without atomics and without colour phases. Each warp of the CTA owns a private
-// accumulator window (the tile plus its halo) and takes chunks of 32
-// consecutive visibilities of the tile's active list; the CTA sums the windows at the
-// end of the tile. Cells are split into 64 classes by (window row mod 8, window column
-// mod 8); lane l owns classes (l / 4, 2 (l % 4) + {0, 1}). A J x J footprint (J <= 8)
-// holds at most one cell of each class, so the lanes of a warp never touch the same
-// cell. Visibilities arrive sorted by base cell inside 8 x 8 super-cells, so runs of
-// them share a "super-row" (one base-cell row, base columns g .. g + 7 with g = 0 mod 8):
-// over a super-row a class has one footprint row and two candidate columns (g + c and
-// g + c + 8), and the lane keeps one running sum per candidate cell in registers,
-// adding them to its window when the super-row changes.
-// Staging (one lane per visibility) writes per-class records that make the lane's work
-// a fixed-address read: for row class r the weight times the value, phi_y(tap) d; for
-// column class c the pair (weight if the class cell is the low candidate, weight if it
-// is the high one), one of them zero.
-constexpr int GW_WARPS = 4;
+// J <= 8 without atomics inside a tile. Warp w of the CTA takes the 8 x 8 super-cells of
+// column w of the tile (T/8 warps), so its points' footprints cover the window columns
+// 8w .. 8w + 15 only: each warp accumulates into a private window of T + 7 rows and 16
+// columns, and the CTA sums the (at most two) windows that cover each cell at the end of
+// the tile. Cells are split into 64 classes by (window row mod 8, window column mod 8);
+// lane l owns classes (l / 4, 2 (l % 4) + {0, 1}). A J x J footprint (J <= 8) holds at
+// most one cell of each class, so the lanes of a warp never touch the same cell. The
+// points of a super-cell arrive sorted by base row: over one base row (a "super-row") a
+// class has one footprint row and two candidate columns (c and c + 8 of the warp's
+// window), and the lane keeps one running sum per candidate cell in registers, adding
+// them to its window when the row changes.
+// Staging (one lane per point, 32 points per chunk) writes per-class records that make
+// the lane's work a fixed-address read: for row class r the weight times the value,
+// phi_y(tap) d; for column class c the pair (weight if the class cell is the low
+// candidate, weight if it is the high one), one of them zero.
+constexpr int GW_MAXW = 16;    // warps per CTA: one per super-cell column (tile <= 128)
 constexpr int GW_RREC = 9;     // row records per staged point (8, padded against bank conflicts)
 constexpr int GW_CREC = 20;    // column record reals per staged point (16, padded, 16-byte rows)
+constexpr int GW_WP = 18;      // window pitch (complex): the 16 columns of one super-cell column's footprints,
+                               // padded so that the 8 rows a warp's flush touches start in distinct banks
 
 template <typename R> __device__ __forceinline__ void ld4(const R* p, R& a, R& b, R& c, R& d) {
     if constexpr (sizeof(R) == 4) {
@@ -452,13 +422,14 @@ template <typename C2> __device__ __forceinline__ void add2(C2* p, C2 a, C2 b) {
     }
 }
 
+// Shared memory of one CTA of nw warps (ms: most segments of a tile).
 template <typename R>
-__host__ __device__ constexpr size_t grid8w_smem(int T, int ms) {
-    return (size_t)GW_WARPS * (T + 7) * (T + 8 > 16 ? T + 8 : 16) * 2 * sizeof(R)   // windows
-           + (size_t)GW_WARPS * 32 * (GW_RREC * 2 + GW_CREC) * sizeof(R)        // records
-           + (size_t)ms * sizeof(R)                                             // active segment scales
-           + (size_t)GW_WARPS * 32 * sizeof(int)                                // super-row keys
-           + (size_t)(3 * ms + 1) * sizeof(int);                                // active segment lists
+__host__ __device__ constexpr size_t grid8w_smem(int T, int nw, int ms) {
+    return (size_t)nw * (T + 7) * GW_WP * 2 * sizeof(R)                       // windows
+           + (size_t)nw * 32 * (GW_RREC * 2 + GW_CREC) * sizeof(R)           // records
+           + (size_t)nw * (ms * (T / 8 > 0 ? T / 8 : 1) + 1) * sizeof(R)      // range scales
+           + (size_t)nw * (2 * (ms * (T / 8 > 0 ? T / 8 : 1)) + 1) * sizeof(int)   // range starts, prefixes
+           + (size_t)(2 * ms + 1) * sizeof(int);                              // active segment lists
 }
 
 // The raw inputs of one staged point, loaded a chunk ahead.
@@ -469,13 +440,13 @@ template <typename R> struct GridIn {
 };
 
 template <typename R, int MODE>
-__device__ __forceinline__ void grid_load(GridIn<R>& in, int pos, int& j, const int* act_pre, const int* act_start,
-                                          const R* act_scale, const cplx_t<R>* __restrict__ src,
+__device__ __forceinline__ void grid_load(GridIn<R>& in, int pos, int& j, const int* rpre, const int* rstart,
+                                          const R* rscale, const cplx_t<R>* __restrict__ src,
                                           const cplx_t<R>* __restrict__ rbuf, const cplx_t<R>* __restrict__ v,
                                           const int32_t* __restrict__ cell, const R* __restrict__ fxs,
                                           const R* __restrict__ fys, const int32_t* __restrict__ perm) {
-    while (act_pre[j + 1] <= pos) ++j;
-    const int m = act_start[j] + pos - act_pre[j];
+    while (rpre[j + 1] <= pos) ++j;
+    const int m = rstart[j] + pos - rpre[j];
     in.m = m;
     in.fx = fxs[m];
     in.fy = fys[m];
@@ -483,44 +454,44 @@ __device__ __forceinline__ void grid_load(GridIn<R>& in, int pos, int& j, const 
     if (MODE == 1) {
         in.a = rbuf[m];
         in.b = v[m];
-        in.sc = act_scale[j];
+        in.sc = rscale[j];
     } else {
         in.a = src[perm[m]];
     }
 }
 
 template <typename R, int J, int MODE>
-__global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
+__global__ void __launch_bounds__(GW_MAXW * 32) k_grid8w(
     const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf, cplx_t<R>* __restrict__ v,
     const R* __restrict__ scale, const int32_t* __restrict__ active, const int32_t* __restrict__ cell,
     const R* __restrict__ fxs, const R* __restrict__ fys, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_block,
-    const int32_t* __restrict__ tile_seg_start, const int32_t* __restrict__ list, const int32_t* __restrict__ count,
-    cplx_t<R>* __restrict__ U, int max_segs, Geo g, R two_over_j, R beta, const KbPoly kp,
-    int* __restrict__ next_tile, int batch, int64_t istride, int64_t ustride) {
+    const int32_t* __restrict__ tile_seg_start, const int32_t* __restrict__ sc_start,
+    const int32_t* __restrict__ list, const int32_t* __restrict__ count, cplx_t<R>* __restrict__ U, int max_segs,
+    Geo g, R two_over_j, R beta, const KbPoly kp, int* __restrict__ next_tile, int batch, int64_t istride,
+    int64_t ustride) {
     static_assert(J <= 8 && J % 2 == 0, "class ownership needs J <= 8");
     using C2 = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    // window rows T + 7 and pitch max(T + 8, 16): every class cell a lane can name (rows
-    // r0 .. r0 + 7, columns up to g + 15) lies inside its own warp's window, even where the
-    // footprint is narrower than 8 (J < 8) and the extra cells only ever receive zeros
-    const int T = g.tile, E = g.ext, EP = T + 8 > 16 ? T + 8 : 16, WS = (T + 7) * EP;
+    const int T = g.tile, E = g.ext, WR = T + 7, WS = WR * GW_WP;
+    const int nsd = T / 8 > 0 ? T / 8 : 1, nsc = nsd * nsd;    // super-cells per side, per tile
+    const int nw = blockDim.x >> 5;                             // = nsd
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C2* wins = reinterpret_cast<C2*>(smraw);                               // [GW_WARPS][T + 7][EP]
+    const int rcap = max_segs * nsd;                            // ranges a warp can hold
+    C2* wins = reinterpret_cast<C2*>(smraw);                    // [nw][WR][GW_WP]
     C2* win = wins + (size_t)warp * WS;
-    C2* rrec_all = wins + (size_t)GW_WARPS * WS;                           // [GW_WARPS][32][GW_RREC]
-    R* crec_all = reinterpret_cast<R*>(rrec_all + GW_WARPS * 32 * GW_RREC); // [GW_WARPS][32][GW_CREC]
-    R* act_scale = crec_all + GW_WARPS * 32 * GW_CREC;                     // [max_segs]
-    int* skey_all = reinterpret_cast<int*>(act_scale + max_segs);          // [GW_WARPS][32]
-    int* act_seg = skey_all + GW_WARPS * 32;                               // [max_segs]
-    int* act_pre = act_seg + max_segs;                                     // [max_segs + 1]
-    int* act_start = act_pre + max_segs + 1;                               // [max_segs]
-    C2* rrec = rrec_all + warp * 32 * GW_RREC;
-    R* crec = crec_all + warp * 32 * GW_CREC;
-    int* skey = skey_all + warp * 32;
-    __shared__ int nact_s;
+    C2* rrec = wins + (size_t)nw * WS + (size_t)warp * 32 * GW_RREC;
+    R* crec = reinterpret_cast<R*>(wins + (size_t)nw * WS + (size_t)nw * 32 * GW_RREC) + (size_t)warp * 32 * GW_CREC;
+    R* rscale = reinterpret_cast<R*>(wins + (size_t)nw * WS + (size_t)nw * 32 * GW_RREC) + (size_t)nw * 32 * GW_CREC +
+                (size_t)warp * (rcap + 1);
+    int* ints = reinterpret_cast<int*>(reinterpret_cast<R*>(wins + (size_t)nw * WS + (size_t)nw * 32 * GW_RREC) +
+                                       (size_t)nw * 32 * GW_CREC + (size_t)nw * (rcap + 1));
+    int* rstart = ints + warp * (2 * rcap + 1);
+    int* rpre = rstart + rcap;                                  // [rcap + 1]
+    int* act_seg = ints + nw * (2 * rcap + 1);
+    int* act_pre = act_seg + max_segs;
+    __shared__ int nact_s, tile_s;
     const int lcy = lane >> 2, lcx = (lane & 3) * 2;
-    __shared__ int tile_s;
     const int n = *count;
     for (;;) {
         // tiles are taken from the heaviest-first list one at a time by whichever CTA is free
@@ -537,28 +508,47 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
         const int seg0 = tile_seg_start[t], nseg_t = tile_seg_start[t + 1] - seg0;
         list_active_segments(seg0, nseg_t, seg_block, MODE == 1 ? active : nullptr, seg_start, act_seg, act_pre,
                              &nact_s);
-        if (warp == 0) {
-            __syncwarp();
-            for (int k = lane; k < nact_s; k += 32) {
-                act_start[k] = seg_start[act_seg[k]];
-                if (MODE == 1) act_scale[k] = scale[seg_block[act_seg[k]]];
-            }
-        }
         for (int i = lane; i < WS; i += 32) win[i] = mk<C2>(R(0), R(0));
         __syncthreads();
-        const int total = act_pre[nact_s];
-        // chunks of 32 consecutive points, chunk k to warp k mod GW_WARPS (a fixed
-        // assignment, so the summation order and the result do not vary between runs)
+        // this warp's ranges: the super-cells of column `warp` of every active segment
+        const int nact = nact_s, nr = nact * nsd;
+        if (lane == 0) rpre[0] = 0;
+        for (int base = 0; base < nr; base += 32) {
+            const int k = base + lane;
+            int len = 0, st0 = 0;
+            R scv = R(0);
+            if (k < nr) {
+                const int jj = k / nsd, srow = k - jj * nsd;
+                const int sg = act_seg[jj];
+                const int sc = srow * nsd + warp;
+                st0 = sc_start[(int64_t)sg * (nsc + 1) + sc];
+                len = sc_start[(int64_t)sg * (nsc + 1) + sc + 1] - st0;
+                if (MODE == 1) scv = scale[seg_block[sg]];
+            }
+            int incl = len;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int yv = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += yv;
+            }
+            const int before = base > 0 ? rpre[base] : 0;
+            __syncwarp();
+            if (k < nr) {
+                rstart[k] = st0;
+                rscale[k] = scv;
+                rpre[k + 1] = before + incl;
+            }
+            __syncwarp();
+        }
+        const int total = nr > 0 ? rpre[nr] : 0;
+        // chunks of 32 consecutive points of the warp's ranges
         const int nchunk = (total + 31) >> 5;
-        int j = 0;            // this lane's segment cursor (its positions only grow)
-        int mykey = -1;       // super-row of this lane's staged point
+        int j = 0;            // this lane's range cursor (its positions only grow)
         GridIn<R> in{};
-        int chunk = warp;
-        if (chunk < nchunk && chunk * 32 + lane < total)
-            grid_load<R, MODE>(in, chunk * 32 + lane, j, act_pre, act_start, act_scale, simg, rbuf, v, cell, fxs,
-                               fys, perm);
-        for (; chunk < nchunk; chunk += GW_WARPS) {
+        if (nchunk > 0 && lane < total)
+            grid_load<R, MODE>(in, lane, j, rpre, rstart, rscale, simg, rbuf, v, cell, fxs, fys, perm);
+        for (int chunk = 0; chunk < nchunk; ++chunk) {
             const int fill = min(32, total - chunk * 32);
+            int mykey = -1;   // footprint row of this lane's staged point
             if (lane < fill) {
                 C2 d;
                 if (MODE == 1) {
@@ -578,32 +568,30 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
                     const R wv = b < J ? wy[b] : R(0);
                     rr[(r0 + b) & 7] = mk<C2>(wv * d.x, wv * d.y);
                 }
-                const int gam = c0 & 7;
+                const int gam = c0 & 7;                             // c0 = 8 warp + gam
                 R* cr = crec + lane * GW_CREC;
 #pragma unroll
                 for (int a = 0; a < 8; ++a) {
                     const R wv = a < J ? wx[a] : R(0);
-                    const int sidx = gam + a;                           // column offset from g
+                    const int sidx = gam + a;                       // column in the warp's window
                     *reinterpret_cast<C2*>(cr + 2 * (sidx & 7)) = sidx >= 8 ? mk<C2>(R(0), wv) : mk<C2>(wv, R(0));
                 }
-                mykey = (r0 << 16) | (c0 & ~7);
+                mykey = r0;
             }
             // the next chunk's loads go out now and land while this one is accumulated
-            const int nxt = chunk + GW_WARPS;
-            if (nxt < nchunk && nxt * 32 + lane < total)
-                grid_load<R, MODE>(in, nxt * 32 + lane, j, act_pre, act_start, act_scale, simg, rbuf, v, cell,
-                                   fxs, fys, perm);
+            const int nxt = (chunk + 1) * 32 + lane;
+            if (nxt < total)
+                grid_load<R, MODE>(in, nxt, j, rpre, rstart, rscale, simg, rbuf, v, cell, fxs, fys, perm);
             __syncwarp();
-            // runs of consecutive points with the same super-row: one set of running sums
+            // runs of consecutive points with the same footprint row: one set of running sums
             // per run, added to the window at its end
-            const int myk = lane < fill ? mykey : -1;
-            const int prevk = __shfl_up_sync(0xffffffffu, myk, 1);
-            unsigned starts = __ballot_sync(0xffffffffu, lane < fill && (lane == 0 || myk != prevk));
+            const int prevk = __shfl_up_sync(0xffffffffu, mykey, 1);
+            unsigned starts = __ballot_sync(0xffffffffu, lane < fill && (lane == 0 || mykey != prevk));
             while (starts) {
                 const int q0 = __ffs(starts) - 1;
                 starts &= starts - 1;
                 const int q1 = starts ? __ffs(starts) - 1 : fill;
-                const int key = __shfl_sync(0xffffffffu, myk, q0);
+                const int r0 = __shfl_sync(0xffffffffu, mykey, q0);
                 // the run's first point starts the running sums, the others add to them two at a time
                 C2 lo0, hi0, lo1, hi1;
                 {
@@ -631,20 +619,20 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_grid8w(
                     lo0.x += wl0 * ry.x; lo0.y += wl0 * ry.y; hi0.x += wh0 * ry.x; hi0.y += wh0 * ry.y;
                     lo1.x += wl1 * ry.x; lo1.y += wl1 * ry.y; hi1.x += wh1 * ry.x; hi1.y += wh1 * ry.y;
                 }
-                const int r0 = key >> 16, g0 = key & 0xFFFF;
-                C2* cp = win + (r0 + ((lcy - r0) & 7)) * EP + g0 + lcx;
+                C2* cp = win + (r0 + ((lcy - r0) & 7)) * GW_WP + lcx;
                 add2(cp, lo0, lo1);
                 add2(cp + 8, hi0, hi1);
             }
             __syncwarp();
         }
         __syncthreads();
-        // U += the sum of the warps' windows (tile and halo)
+        // U += the windows (tile and halo): column ex of the tile window lies in warp
+        // ex/8's window (local column ex mod 8) and in warp ex/8 - 1's (local ex mod 8 + 8)
         add_window<R>(Uimg, oy, ox, g, [&](int ey, int ex) {
-            const int kk = ey * EP + ex;
-            C2 sum = wins[kk];
-#pragma unroll
-            for (int ww = 1; ww < GW_WARPS; ++ww) sum = cadd(sum, wins[(size_t)ww * WS + kk]);
+            const int w0 = ex >> 3, lc = ex & 7;
+            C2 sum = mk<C2>(R(0), R(0));
+            if (w0 < nw) sum = wins[(size_t)w0 * WS + ey * GW_WP + lc];
+            if (w0 >= 1) sum = cadd(sum, wins[(size_t)(w0 - 1) * WS + ey * GW_WP + lc + 8]);
             return sum;
         });
         __syncthreads();
@@ -745,17 +733,18 @@ static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const D
     const int32_t* act = a ? a->block_active : nullptr;
     cudaError_t e;
     if constexpr (J <= 8) {
-        const size_t smem8 = grid8w_smem<R>(g.tile, ms);
+        const int nw = std::max(1, g.tile / SC);
+        const size_t smem8 = grid8w_smem<R>(g.tile, nw, ms);
         if ((e = ensure_smem(k_grid8w<R, J, MODE>, smem8))) return e;
         int per_sm = 0;
-        int ctas8 = std::min(g.ntiles, p->num_sms * 8);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid8w<R, J, MODE>, GW_WARPS * 32, smem8) ==
+        int ctas8 = std::min(g.ntiles * batch, p->num_sms * 16);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid8w<R, J, MODE>, nw * 32, smem8) ==
                 cudaSuccess && per_sm > 0)
             ctas8 = std::min(ctas8, per_sm * p->num_sms);
-        k_grid8w<R, J, MODE><<<ctas8, GW_WARPS * 32, smem8, s>>>(
+        k_grid8w<R, J, MODE><<<ctas8, nw * 32, smem8, s>>>(
             src, rb, vv, (const R*)p->blk_scale, act, p->cell, (const R*)p->fx, (const R*)p->fy, p->perm,
-            p->seg_start, p->seg_block, p->tile_seg_start, tiles, count, U, ms, g, toj, beta, p->kbpoly, next_tile,
-            batch, (int64_t)p->M, (int64_t)g.Kx * g.Ky);
+            p->seg_start, p->seg_block, p->tile_seg_start, p->seg_sc_start, tiles, count, U, ms, g, toj, beta,
+            p->kbpoly, next_tile, batch, (int64_t)p->M, (int64_t)g.Kx * g.Ky);
     } else {
         const size_t smem = (size_t)2 * g.ext * g.ext * sizeof(R) + lists;
         if ((e = ensure_smem(k_grid<R, J, MODE>, smem))) return e;

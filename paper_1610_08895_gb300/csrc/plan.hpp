@@ -77,6 +77,8 @@ struct pd_plan {
     int32_t* seg_block = nullptr;  // [nseg]
     int32_t* tile_seg_start = nullptr;  // [ntiles + 1]
     int nsc_side = 0;                      // super-cells per tile side (tile / SC)
+    int32_t* seg_sc_start = nullptr;       // [nseg][nsc_side^2 + 1] super-cell starts inside each segment
+    std::vector<int32_t> h_sc_start;       // (host, only during plan construction)
     int max_tile_segs = 0;                 // most (tile, block) segments in one tile
     pdgb::KbPoly kbpoly{};
     int32_t* block_seg_start = nullptr;    // [d + 1] into block_seg_list
