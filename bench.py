@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-operators", action="store_true")
+    ap.add_argument("--no-csr", action="store_true")
+    ap.add_argument("--no-sara", action="store_true")
+    ap.add_argument("--csr-steps", type=int, default=20)
+    ap.add_argument("--g-mode", default="on_the_fly", choices=["on_the_fly", "csr"],
+                    help="form of G for --profile-run")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0, help="gridding tile edge (0: the plan's default)")
     ap.add_argument("--profile-run", type=int, default=0,
@@ -271,7 +276,10 @@ def run_cufft(n, stream, reps=20):
             "ifft2_ms": round(_time_ms(lambda: torch.fft.ifft2(g), reps, stream), 4)}
 
 
-KERNELS_PER_ITER = lambda L: 1 + 2 + 2 + 2 + (1 + L) + (L - 1 + 1) + 2 + 1   # noqa: E731
+# our kernels per iteration: draws; 2 forward passes; degridding + block norms; 4 gridding
+# colour launches; L analysis levels + the Dirac basis; L synthesis levels + the ordered
+# sum; 2 inverse passes; the primal norm sums
+KERNELS_PER_ITER = lambda L: 1 + 2 + 2 + 4 + (L + 1) + (L + 1) + 2 + 1   # noqa: E731
 
 
 # ---------------------------------------------------------------------------------------------
@@ -430,6 +438,16 @@ def run_ours(args):
         fp64["batched_graph"]["form"] = "FP64 bulk data in the batched kernels, one CUDA graph per iteration"
         plan64.close()
 
+    # ---- the same workload with G held as a sparse matrix (CSR, built on the device at plan time)
+    csr = None
+    if not args.no_csr:
+        csr = run_csr(args, cfg, uv, blk, d, tile, y, eps, kw, sizes, stream)
+
+    # ---- the reweighted prior (SARA): the same iterations with per-coefficient weights
+    sara = None
+    if not args.no_sara:
+        sara = run_sara(args, plan, st, kw, stream)
+
     # ---- errors of this run's results against the FP64 oracle on sampled outputs
     errors = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -453,11 +471,84 @@ def run_ours(args):
                        "graph": "one CUDA graph per iteration, replayed", "setup_s": round(setup_s, 1),
                        "plan": info},
             "roofline": roofline, "kernels": kernels, "clocks": clk.summary(), "e2e": e2e,
-            "fp64": fp64, "operators": operators, "cpu_baseline": cpu, "errors": errors,
+            "fp64": fp64, "csr": csr, "sara": sara, "operators": operators, "cpu_baseline": cpu, "errors": errors,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_csr(args, cfg, uv, blk, d, tile, y, eps, kw, sizes, stream):
+    """FP32 batched graph iterations with G stored as a sparse matrix (J^2 column/weight
+    pairs per visibility) instead of evaluated in the kernels, and the degridding and
+    gridding kernel times with their algorithmic bytes (the stored entries dominate)."""
+    import torch
+    from paper_1610_08895_gb300.api import Plan, State
+    n, J = cfg["n"], cfg["J"]
+    plan = Plan(n, n, uv, blk, d, kernel_width=J, basis_ids=cfg["bases"], levels=cfg["levels"],
+                precision="f32", tile=tile, g_mode="csr")
+    info = plan.info()
+    st = State(plan)
+    st.pd_state_set_data(y, eps)
+    st.pd_iterate(3, use_graph=True, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st.pd_iterate(args.csr_steps, use_graph=True, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st.profile(reset=True)
+    m_act, t_act, reps = 0.0, 0.0, 5
+    for _ in range(reps):
+        st.pd_iterate(1, profile=True, **kw)
+        rep = st.report()
+        m_act += float(sizes[rep["block_active"]].sum())
+        t_act += rep["active_tiles"] / info["kx"] / info["ky"] * info["tile"] ** 2
+    prof = st.profile()
+    K = 4 * n * n
+    per_vis = 24 + 8 * J * J             # y, v in, r out (or r, v in, v out) + the stored row of G
+    alg = {"degrid_dual": per_vis * m_act / reps + 8 * K * t_act / reps,
+           "grid_dual": per_vis * m_act / reps + 16 * K * t_act / reps}
+    kernels = {}
+    for name in ("degrid_dual", "grid_dual"):
+        tot, cnt = prof.get(name, (0.0, 0))
+        if cnt:
+            avg = tot / cnt
+            kernels[name] = {"ms": round(avg, 4), "GBps": round(alg[name] / (avg / 1e3) / 1e9, 1),
+                             "algorithmic_bytes_per_launch": int(alg[name])}
+    st.close()
+    out = {"value": round(args.csr_steps / (ms / 1e3), 3), "unit": "PD iters/s",
+           "ms_per_step": round(ms / args.csr_steps, 4), "steps": args.csr_steps,
+           "g_bytes": int(J * J * 8 * cfg["m"]), "device_bytes": info.get("device_bytes"),
+           "kernels": kernels,
+           "form": "FP32 batched graph; G as CSR with J^2 (int32 cell, fp32 weight) entries per visibility"}
+    plan.close()
+    return out
+
+
+def run_sara(args, plan, st, kw, stream, steps=20):
+    """Batched graph iterations with the reweighted prior: weights from the current
+    iterate (pd_sara_weights), then timed iterations that read them in step 13."""
+    import torch
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    w = plan.pd_sara_weights(st.x(), 1e-3)
+    t0.record(stream)
+    plan.pd_sara_weights(st.x(), 1e-3, weights=w)
+    t1.record(stream)
+    st.pd_iterate(3, use_graph=True, weights=w, **kw)
+    torch.cuda.synchronize()
+    rule_ms = t0.elapsed_time(t1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st.pd_iterate(steps, use_graph=True, weights=w, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": round(steps / (ms / 1e3), 3), "unit": "PD iters/s", "ms_per_step": round(ms / steps, 4),
+            "steps": steps, "reweight_ms": round(rule_ms, 4),
+            "form": "FP32 batched graph, step 13 with per-coefficient weights W = delta/(delta + |Psi^H x|)"}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -476,7 +567,7 @@ def run_profile_target(args):
     d = int(blk.max()) + 1
     b = len(cfg["bases"])
     plan = Plan(n, n, uv, blk, d, kernel_width=cfg["J"], basis_ids=cfg["bases"], levels=cfg["levels"],
-                precision="f32", tile=args.tile)
+                precision="f32", tile=args.tile, g_mode=args.g_mode)
     st = State(plan)
     st.pd_state_set_data(torch.tensor(10.0 * noise, dtype=torch.complex64, device="cuda"), np.full(d, 30.0))
     x0 = torch.tensor(x_true, dtype=torch.float32, device="cuda")

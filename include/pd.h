@@ -73,6 +73,16 @@ typedef struct pd_state pd_state;
  * levels        wavelet levels 1 <= L <= 13 with nx >> L >= 1 and ny >> L >= 1.
  * precision     PD_F32 (complex64 bulk data, FP64 reductions) or PD_F64.
  * tile          gridding tile edge in cells (power of two, >= J); 0 = choose.
+ * g_mode        PD_G_ON_THE_FLY: the interpolation weights of G are evaluated in the
+ *               kernels; PD_G_CSR: G is built once at plan time, on the device, as a
+ *               sparse matrix in CSR form (Sec. 2: G is sparse with J^2 entries per
+ *               row): row m (one visibility) holds J^2 (column, weight) pairs, the
+ *               column packing the grid cell as (ky << 16 | kx) and the weight the
+ *               FP64 product of the two axis weights rounded once to the working
+ *               precision; every row has J^2 entries, so the row pointer is m J^2.
+ *               J^2 (4 + sizeof real) bytes per visibility (8.6 GB at 16.8M
+ *               visibilities, J = 8, FP32), held by the plan. Both modes apply the
+ *               same operator (to rounding); CSR needs J <= 8 (PD_ENOTSUP otherwise).
  */
 typedef struct {
     int32_t nx, ny;
@@ -88,7 +98,10 @@ typedef struct {
     int32_t levels;
     int32_t precision;
     int32_t tile;
+    int32_t g_mode;
 } pd_plan_desc;
+
+typedef enum { PD_G_ON_THE_FLY = 0, PD_G_CSR = 1 } pd_g_mode;
 
 /*
  * Build a plan: validate the description, sort the visibilities by gridding
@@ -214,6 +227,18 @@ pd_status pd_state_set_data(pd_plan* plan, pd_state* st, const void* y, const do
                             void* stream);
 
 /*
+ * Weights of the reweighted analysis prior (SARA, Sec. 2, which cites but does not
+ * define it): weights = delta / (delta + |Psi^H x|) per coefficient of the normalised
+ * dictionary Psi^H x (the coefficients pd_apply_psi_adj writes), the usual reweighted-l1
+ * rule. x: device real [ny][nx]; weights: device real [nbases][ny][nx], caller-owned,
+ * written on `stream` (asynchronous). delta > 0 sets the scale below which a coefficient
+ * counts as zero; the outer loop that recomputes the weights from the current x and
+ * lowers delta between runs of pd_iterate is the caller's. Uses the plan's wavelet
+ * scratch like pd_apply_psi_adj. Errors: PD_EINVAL (null, delta <= 0), PD_ECUDA.
+ */
+pd_status pd_sara_weights(pd_plan* plan, const void* x, double delta, void* weights, void* stream);
+
+/*
  * Start values of Algorithm 1 (step 1: x^(0), x~^(0), s^(0), v^(0) are given), for a
  * warm start or a resumed reconstruction. Call after pd_state_set_data (it keeps y
  * and eps). x0, x_tilde0: device real [ny][nx]; s0: device real [b][ny][nx]
@@ -250,6 +275,13 @@ typedef struct {
                                       synthesis once per active basis; same results up to rounding
                                       order. Needs adaptive = 0 and use_graph = 0; synchronises
                                       `stream` after every iteration. */
+    const void* sparsity_weights;  /* NULL: the l1 prior of Sec. 2 (problem analysis-l1). Else device
+                                      real [nbases][ny][nx], packed like s, caller-owned: the
+                                      per-coefficient weights W of the reweighted prior of SARA
+                                      (Sec. 2), min ||W Psi^H x||_1, whose step-13 threshold is
+                                      kappa * psi_norm * W; values in (0, 1] (pd_sara_weights).
+                                      Read by every iteration; a graph is re-captured when the
+                                      pointer changes, not when the values do. */
 } pd_params;
 
 /*

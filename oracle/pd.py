@@ -19,6 +19,13 @@ notation. Plain choices where the paper is silent:
   ||Phi_i x^(t) - y_i|| of the primal iterate after every iteration, for all
   blocks (Sec. 4 defines c_i on Phi_i x^(t); this costs one full Phi per iteration).
 * The stopping rule "until convergence" (step 19) is a fixed iteration count.
+* Reweighted analysis prior (SARA, cited in Sec. 2 but not defined there): with
+  weights W (one per coefficient of Psi^H x, all in (0, 1]) the objective is
+  ||W Psi^H x||_1, and step 13 becomes the weighted soft threshold of size
+  kappa ||Psi||_S W. ``sara_weights`` gives the usual reweighting rule
+  W = delta / (delta + |Psi^H x|) (reweighted l1, Candes, Wakin and Boyd 2008, as used
+  by SARA) for the caller's delta; the outer loop that recomputes W and lowers delta
+  between runs of Algorithm 1 is the caller's.
 """
 import numpy as np
 
@@ -101,8 +108,9 @@ class PDState:
 
 
 def pd_iteration(problem, st, tau, sigma, varsigma, kappa, psi_norm, seed,
-                 p_block, p_basis, adaptive=None):
-    """One iteration t of Algorithm 1 (steps 3-18). Returns the active sets drawn."""
+                 p_block, p_basis, adaptive=None, weights=None):
+    """One iteration t of Algorithm 1 (steps 3-18). Returns the active sets drawn.
+    weights: None, or [b][ny][nx] per-coefficient weights of the reweighted prior."""
     st.t += 1
     t = st.t
     # step 3: generate the active set (Sec. 3; Sec. 4 for adaptive p)
@@ -128,7 +136,7 @@ def pd_iteration(problem, st, tau, sigma, varsigma, kappa, psi_norm, seed,
         if not active_basis[k]:
             continue
         w = _wav.psi_j_adj(st.x_tilde, j, problem.levels) / np.sqrt(b)            # (Psi^H x~)_j
-        st.s[k] = _prox.dual_sparsity_update(st.s[k], w, alpha)
+        st.s[k] = _prox.dual_sparsity_update(st.s[k], w, alpha if weights is None else alpha * weights[k])
     # step 14: s~ = Psi s
     s_tilde = problem.psi(st.s)
     # step 9 / 17: sum_i M_i^T v~_i = G^T v, then Z^T F^H
@@ -145,14 +153,20 @@ def pd_iteration(problem, st, tau, sigma, varsigma, kappa, psi_norm, seed,
 
 
 def pd_run(problem, niter, tau, sigma, varsigma, kappa, psi_norm, seed,
-           p_block, p_basis, adaptive=None, state=None):
+           p_block, p_basis, adaptive=None, state=None, weights=None):
     """Run ``niter`` iterations of Algorithm 1; returns (state, list of active sets)."""
     st = PDState(problem) if state is None else state
     draws = []
     for _ in range(niter):
         draws.append(pd_iteration(problem, st, tau, sigma, varsigma, kappa, psi_norm, seed,
-                                  p_block, p_basis, adaptive))
+                                  p_block, p_basis, adaptive, weights))
     return st, draws
+
+
+def sara_weights(problem, x, delta):
+    """Reweighting rule of the reweighted analysis prior: W = delta / (delta + |Psi^H x|),
+    per coefficient of the normalised dictionary Psi = b^{-1/2} [Psi_1 ... Psi_b]."""
+    return delta / (delta + np.abs(problem.psi_adj(x)))
 
 
 def objective(problem, x):

@@ -6,7 +6,8 @@
   coefficients; |z| = alpha and z = 0 both give 0.
 * ``proj_positive``: P_C of eq. (proj-plus), Sec. 3: Re(z) where Re(z) > 0, else 0.
 * ``dual_data_update``: step 8 of Algorithm 1, v + Gb - P_B(v + Gb).
-* ``dual_sparsity_update``: step 13 of Algorithm 1, s + w - S_alpha(s + w).
+* ``dual_sparsity_update``: step 13 of Algorithm 1, s + w - S_alpha(s + w)
+  (alpha scalar, or per coefficient for the reweighted prior).
 """
 import numpy as np
 
@@ -21,12 +22,17 @@ def proj_l2ball(z, y, eps):
 
 
 def soft_threshold(z, alpha):
-    """S_alpha(z)_k = z_k {|z_k| - alpha}_+ / |z_k| for |z_k| > 0, else 0 (eq. prox-L1)."""
+    """S_alpha(z)_k = z_k {|z_k| - alpha_k}_+ / |z_k| for |z_k| > 0, else 0 (eq. prox-L1).
+
+    alpha is a scalar, or an array of z's shape for the weighted l1 norm
+    sum_k alpha_k |z_k| (the reweighted prior of SARA, Sec. 2), whose proximity
+    operator is the same componentwise shrinkage with per-coefficient sizes."""
     z = np.asarray(z, dtype=np.float64)
+    a = np.broadcast_to(np.asarray(alpha, dtype=np.float64), z.shape)
     mag = np.abs(z)
     out = np.zeros_like(z)
     nz = mag > 0
-    out[nz] = z[nz] * np.maximum(mag[nz] - alpha, 0.0) / mag[nz]
+    out[nz] = z[nz] * np.maximum(mag[nz] - a[nz], 0.0) / mag[nz]
     return out
 
 

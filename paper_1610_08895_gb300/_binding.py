@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpdgb.so")
 
 PD_OK, PD_EINVAL, PD_ENOMEM, PD_ECUDA, PD_ETIMEOUT, PD_ENOTCONV, PD_ENOTSUP = range(7)
 PD_F32, PD_F64 = 0, 1
+PD_G_ON_THE_FLY, PD_G_CSR = 0, 1
 STATUS_NAMES = {0: "PD_OK", 1: "PD_EINVAL", 2: "PD_ENOMEM", 3: "PD_ECUDA", 4: "PD_ETIMEOUT",
                 5: "PD_ENOTCONV", 6: "PD_ENOTSUP"}
 
@@ -31,7 +32,8 @@ class PdPlanDesc(ctypes.Structure):
                 ("nvis", ctypes.c_int64), ("uv", ctypes.c_void_p), ("nblocks", ctypes.c_int32),
                 ("block_of_vis", ctypes.c_void_p), ("kernel_width", ctypes.c_int32),
                 ("kb_beta", ctypes.c_double), ("nbases", ctypes.c_int32), ("basis_ids", ctypes.c_void_p),
-                ("levels", ctypes.c_int32), ("precision", ctypes.c_int32), ("tile", ctypes.c_int32)]
+                ("levels", ctypes.c_int32), ("precision", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("g_mode", ctypes.c_int32)]
 
 
 class PdParams(ctypes.Structure):
@@ -40,7 +42,8 @@ class PdParams(ctypes.Structure):
                 ("p_block", ctypes.c_void_p), ("p_basis", ctypes.c_void_p), ("adaptive", ctypes.c_int32),
                 ("adapt_n", ctypes.c_double), ("adapt_p_min", ctypes.c_double),
                 ("adapt_p_max", ctypes.c_double), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("adapt_exact", ctypes.c_int32), ("per_block", ctypes.c_int32)]
+                ("adapt_exact", ctypes.c_int32), ("per_block", ctypes.c_int32),
+                ("sparsity_weights", ctypes.c_void_p)]
 
 
 _lib = None
@@ -56,6 +59,7 @@ _SIGS = {
     "pd_apply_phi": ([_VP, _VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
     "pd_apply_phi_adj": ([_VP, _VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
     "pd_apply_psi_adj": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "pd_sara_weights": ([_VP, _VP, ctypes.c_double, _VP, _VP], ctypes.c_int),
     "pd_apply_psi": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "pd_apply_psi_adj_noalloc": ([_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int32,
                                   ctypes.c_int32, _VP], ctypes.c_int),

@@ -34,11 +34,18 @@ def _need(t, dtype, shape, name):
         raise ValueError(f"{name} must be contiguous")
 
 
+_G_MODE = {"on_the_fly": B.PD_G_ON_THE_FLY, "csr": B.PD_G_CSR}
+
+
 class Plan:
-    """pd_plan_create: image size, oversampling 2, uv points, blocks, kernel width, bases."""
+    """pd_plan_create: image size, oversampling 2, uv points, blocks, kernel width, bases.
+
+    g_mode "on_the_fly" evaluates the Kaiser-Bessel weights of G in the kernels; "csr"
+    builds G once as a sparse matrix on the device (J^2 column/weight pairs per
+    visibility, J <= 8) and reads it in every application."""
 
     def __init__(self, nx, ny, uv, block_of_vis, nblocks, kernel_width=8, basis_ids=(0,), levels=1,
-                 precision="f32", tile=0, kb_beta=0.0):
+                 precision="f32", tile=0, kb_beta=0.0, g_mode="on_the_fly"):
         B.load()
         self.nx, self.ny = int(nx), int(ny)
         self.uv = np.ascontiguousarray(uv, dtype=np.float64)
@@ -51,11 +58,14 @@ class Plan:
         self.prec = {"f32": B.PD_F32, "f64": B.PD_F64}[precision] if isinstance(precision, str) else int(precision)
         self.real_dtype = _REAL[self.prec]
         self.cplx_dtype = _CPLX[self.prec]
+        if g_mode not in _G_MODE:
+            raise ValueError(f"g_mode must be one of {sorted(_G_MODE)}, got {g_mode!r}")
+        self.g_mode = g_mode
         d = B.PdPlanDesc(nx=self.nx, ny=self.ny, osf=2, nvis=self.nvis, uv=self.uv.ctypes.data,
                          nblocks=self.nblocks, block_of_vis=self.block_of_vis.ctypes.data,
                          kernel_width=int(kernel_width), kb_beta=float(kb_beta), nbases=self.nbases,
                          basis_ids=self.basis_ids.ctypes.data, levels=self.levels, precision=self.prec,
-                         tile=int(tile))
+                         tile=int(tile), g_mode=_G_MODE[g_mode])
         h = ctypes.c_void_p()
         B.call("pd_plan_create", ctypes.byref(d), ctypes.byref(h))
         self._h = h
@@ -114,6 +124,15 @@ class Plan:
         _need(coeffs, self.real_dtype, (self.nbases, self.ny, self.nx), "coeffs")
         B.call("pd_apply_psi_adj", self._h, _ptr(x), _ptr(coeffs), _stream())
         return coeffs
+
+    def pd_sara_weights(self, x, delta, weights=None):
+        """pd_sara_weights: delta / (delta + |Psi^H x|) per coefficient, [nbases, ny, nx]."""
+        _need(x, self.real_dtype, (self.ny, self.nx), "x")
+        if weights is None:
+            weights = torch.empty((self.nbases, self.ny, self.nx), dtype=self.real_dtype, device=x.device)
+        _need(weights, self.real_dtype, (self.nbases, self.ny, self.nx), "weights")
+        B.call("pd_sara_weights", self._h, _ptr(x), ctypes.c_double(float(delta)), _ptr(weights), _stream())
+        return weights
 
     def pd_apply_psi(self, coeffs, x=None):
         _need(coeffs, self.real_dtype, (self.nbases, self.ny, self.nx), "coeffs")
@@ -178,14 +197,21 @@ class State:
         B.call("pd_state_set_start", p.handle, self._h, *args, _stream())
 
     def pd_iterate(self, niter, tau, sigma, varsigma, kappa, psi_norm=1.0, seed=0, p_block=None, p_basis=None,
-                   adaptive=None, use_graph=False, profile=False, per_block=False):
+                   adaptive=None, use_graph=False, profile=False, per_block=False, weights=None):
+        """pd_iterate. weights: None (l1 prior) or a device tensor [nbases, ny, nx] of the
+        reweighted prior's per-coefficient weights (kept referenced by the state, since a
+        captured graph reads it on every replay)."""
         p = self.plan
+        if weights is not None:
+            _need(weights, p.real_dtype, (p.nbases, p.ny, p.nx), "weights")
+        self._weights = weights
         pb = np.ascontiguousarray(np.ones(p.nblocks) if p_block is None else p_block, dtype=np.float64)
         ps = np.ascontiguousarray(np.ones(p.nbases) if p_basis is None else p_basis, dtype=np.float64)
         prm = B.PdParams(tau=tau, sigma=sigma, varsigma=varsigma, kappa=kappa, psi_norm=psi_norm, seed=int(seed),
                          p_block=pb.ctypes.data, p_basis=ps.ctypes.data, adaptive=0, adapt_n=0.0,
                          adapt_p_min=0.0, adapt_p_max=0.0, use_graph=int(bool(use_graph)),
-                         profile=int(bool(profile)), per_block=int(bool(per_block)))
+                         profile=int(bool(profile)), per_block=int(bool(per_block)),
+                         sparsity_weights=None if weights is None else weights.data_ptr())
         if adaptive is not None:
             prm.adaptive = 1
             prm.adapt_n = float(adaptive["n"])

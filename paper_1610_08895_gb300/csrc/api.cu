@@ -138,8 +138,12 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
     if (d->kb_beta < 0) return fail(PD_EINVAL, "kb_beta must be >= 0");
     if (d->tile != 0 && (!is_pow2(d->tile) || d->tile < d->kernel_width))
         return fail(PD_EINVAL, "tile must be 0 or a power of two >= kernel_width");
+    if (d->g_mode != PD_G_ON_THE_FLY && d->g_mode != PD_G_CSR)
+        return fail(PD_EINVAL, "g_mode must be PD_G_ON_THE_FLY or PD_G_CSR");
+    if (d->g_mode == PD_G_CSR && d->kernel_width > 8) return fail(PD_ENOTSUP, "the CSR form of G needs J <= 8");
 
     p->prec = d->precision;
+    p->g_mode = d->g_mode;
     p->rsz = p->prec == PD_F64 ? 8 : 4;
     p->csz = 2 * p->rsz;
     Geo& g = p->g;
@@ -390,6 +394,14 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         ALLOC(p->sched, 8);
         CU(cudaMemset(p->ds, 0, (size_t)p->b * N * p->rsz));
     }
+    if (p->g_mode == PD_G_CSR) {
+        const size_t nnz = (size_t)g.J * g.J * (size_t)M;
+        if (dalloc(A, B, &p->csr_col, nnz) != cudaSuccess || dalloc_bytes(A, B, &p->csr_val, nnz * p->rsz) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(PD_ENOMEM, "the CSR form of G does not fit in device memory");
+        }
+        CU(build_csr(p, 0));
+    }
 #undef ALLOC
     CU(cudaDeviceSynchronize());
     return PD_OK;
@@ -480,6 +492,14 @@ extern "C" pd_status pd_apply_psi(pd_plan* p, const void* coeffs, void* x, void*
     if (!p || !x || !coeffs) return fail(PD_EINVAL, "pd_apply_psi: null argument");
     if (p->prec == PD_F64) CU(psi_plain<double>(p, (const double*)coeffs, (double*)x, (cudaStream_t)stream));
     else CU(psi_plain<float>(p, (const float*)coeffs, (float*)x, (cudaStream_t)stream));
+    return PD_OK;
+}
+
+extern "C" pd_status pd_sara_weights(pd_plan* p, const void* x, double delta, void* weights, void* stream) {
+    if (!p || !x || !weights) return fail(PD_EINVAL, "pd_sara_weights: null argument");
+    if (!(delta > 0) || !std::isfinite(delta)) return fail(PD_EINVAL, "pd_sara_weights: delta must be positive and finite");
+    if (p->prec == PD_F64) CU(sara_weights<double>(p, (const double*)x, delta, (double*)weights, (cudaStream_t)stream));
+    else CU(sara_weights<float>(p, (const float*)x, delta, (float*)weights, (cudaStream_t)stream));
     return PD_OK;
 }
 
@@ -712,7 +732,7 @@ static cudaError_t enqueue_dual(pd_plan* p, pd_state* st, const pd_params* prm, 
         if ((e = cudaStreamWaitEvent(ps, st->ev_fork, 0))) return e;
     }
     if ((e = sparsity_dual<R>(p, (const R*)st->xt, (R*)st->s, (R*)st->st, st->basis_active,
-                              prm->kappa * prm->psi_norm, ps)))
+                              prm->kappa * prm->psi_norm, ps, (const R*)prm->sparsity_weights)))
         return e;
     if (concurrent && (e = cudaEventRecord(st->ev_join, ps))) return e;
     if ((e = fwd_fft<R>(p, (const R*)st->xt, (cplx_t<R>*)p->gridb, s))) return e;
@@ -831,7 +851,7 @@ static cudaError_t enqueue_iteration_per_block(pd_plan* p, pd_state* st, const p
     for (int j = 0; j < b; ++j) {
         if (!st->h_actb[j]) continue;
         if ((e = sparsity_dual<R>(p, (const R*)st->xt, (R*)st->s, (R*)st->st, st->pb_eye_bases + (size_t)j * b,
-                                  prm->kappa * prm->psi_norm, s)))
+                                  prm->kappa * prm->psi_norm, s, (const R*)prm->sparsity_weights)))
             return e;
     }
     PrimalArgs pa{prm->tau, prm->sigma, prm->varsigma, st->x, st->xt, st->st, st->prim_part};
@@ -851,6 +871,7 @@ static std::vector<unsigned char> params_key(const pd_plan* p, const pd_params* 
     put(&prm->adaptive, sizeof(int32_t)); put(&prm->adapt_n, sizeof(double));
     put(&prm->adapt_p_min, sizeof(double)); put(&prm->adapt_p_max, sizeof(double));
     put(&prm->adapt_exact, sizeof(int32_t));
+    put(&prm->sparsity_weights, sizeof(void*));
     put(&s, sizeof(s));
     (void)p;
     return k;

@@ -22,94 +22,32 @@
 //   so no two CTAs of a launch touch the same cell of U. No global atomics.
 #include <algorithm>
 
-#include "common.cuh"
-#include "plan.hpp"
+#include "gridding.cuh"
 
 namespace pdgb {
 
-// The J tap weights phi(frac + J/2 - 1 - a) of one axis. FP32: the plan's per-tap
-// Chebyshev interpolants (degree 10, interpolation error ~3e-11 of phi(0), below FP32
-// resolution) in x = 2 frac - 1. phi is even, so tap J-1-a is tap a at -x: with the
-// polynomial split into even and odd parts p = E(x^2) + x O(x^2), one pass gives both
-// E + x O (tap a) and E - x O (tap J-1-a). FP64: I0 itself.
-template <typename R, int J>
-__device__ __forceinline__ void kb_taps(R frac, R* w, R two_over_j, R beta, const KbPoly& kp) {
-    if constexpr (sizeof(R) == 4) {
-        const float x = 2.0f * frac - 1.0f, x2 = x * x;
-#pragma unroll
-        for (int a = 0; a < J / 2; ++a) {
-            float ev = kp.c[a][KB_DEG], od = kp.c[a][KB_DEG - 1];
-#pragma unroll
-            for (int k = KB_DEG - 2; k >= 0; k -= 2) ev = fmaf(ev, x2, kp.c[a][k]);
-#pragma unroll
-            for (int k = KB_DEG - 3; k >= 1; k -= 2) od = fmaf(od, x2, kp.c[a][k]);
-            w[a] = fmaf(x, od, ev);
-            w[J - 1 - a] = fmaf(-x, od, ev);
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < J; ++a) w[a] = kb_weight<R>(frac + R(J / 2 - 1 - a), two_over_j, beta);
-    }
-}
-
-// ---------------------------------------------------------------- active segments
-// Warp 0 lists the tile's segments whose block is active (all of them when active is
-// null) in act_seg[0..nact) and the prefix sums of their lengths in act_pre[0..nact];
-// returns nact to every thread (the caller syncs before use).
-__device__ __forceinline__ void list_active_segments(int seg0, int nseg_t, const int32_t* __restrict__ seg_block,
-                                                     const int32_t* __restrict__ active,
-                                                     const int32_t* __restrict__ seg_start, int* act_seg,
-                                                     int* act_pre, int* nact_out) {
-    if ((threadIdx.x >> 5) != 0) return;
-    const int lane = threadIdx.x & 31;
-    const unsigned below = (1u << lane) - 1u;
-    int nact = 0, total = 0;
-    for (int base = 0; base < nseg_t; base += 32) {
-        const int k = base + lane;
-        const bool ok = k < nseg_t && (active == nullptr || active[seg_block[seg0 + k]]);
-        const int len = ok ? seg_start[seg0 + k + 1] - seg_start[seg0 + k] : 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, ok);
-        int incl = len;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (ok) {
-            const int pos = nact + __popc(bal & below);
-            act_seg[pos] = seg0 + k;
-            act_pre[pos] = total + incl - len;
-        }
-        total += __shfl_sync(0xffffffffu, incl, 31);
-        nact += __popc(bal);
-    }
-    if (lane == 0) { act_pre[nact] = total; *nact_out = nact; }
-}
-
-// Cell (ky, kx) of F Z x from the half grid (columns 0 .. nx, column panels): the image
-// is real, so the columns kx > nx are conj(b[-ky][-kx]).
-template <typename C2>
-__device__ __forceinline__ C2 half_grid_at(const C2* __restrict__ gh, int ky, int kx, const Geo& g) {
-    if (kx <= g.nx) return gh[panel_off(ky, kx, g.Ky)];
-    const C2 v = gh[panel_off((g.Ky - ky) & (g.Ky - 1), g.Kx - kx, g.Ky)];
-    return mk<C2>(v.x, -v.y);
-}
-
 // ---------------------------------------------------------------- degridding
-// Warp-level segmented sum: the lanes with ok add (a, b) to their local segment ls;
-// lane 0 adds each segment's warp total into part[2 ls], part[2 ls + 1] (FP64 slots
-// owned by this warp), always in the same order. The at most 32 terms of one warp are
-// summed in the working precision A (a fixed shuffle tree of non-negative terms:
-// relative error below 6 units of A's rounding), every sum above that in FP64.
-template <typename A>
-__device__ __forceinline__ void warp_seg_add(bool ok, int ls, A a, A b, double* part) {
-    unsigned todo = __ballot_sync(0xffffffffu, ok);
-    while (todo) {
-        const int key = __shfl_sync(0xffffffffu, ls, __ffs(todo) - 1);
-        const bool mine = ok && ls == key;
-        const unsigned mask = __ballot_sync(0xffffffffu, mine);
-        const A x = warp_sum(mine ? a : A(0)), y = warp_sum(mine ? b : A(0));
-        if ((threadIdx.x & 31) == 0) { part[2 * key] += (double)x; part[2 * key + 1] += (double)y; }
-        todo &= ~mask;
+// The global inputs of one point to degrid (MODE 1 also its y and v).
+template <typename R> struct DegridIn {
+    cplx_t<R> yy, vv;
+    R fx, fy;
+    int c, m;
+};
+
+template <typename R, int MODE>
+__device__ __forceinline__ void degrid_load(DegridIn<R>& in, int pos, int& j, const int* act_seg, const int* act_pre,
+                                            const int32_t* __restrict__ seg_start, const int32_t* __restrict__ cell,
+                                            const R* __restrict__ fxs, const R* __restrict__ fys,
+                                            const cplx_t<R>* __restrict__ y, const cplx_t<R>* __restrict__ v) {
+    while (act_pre[j + 1] <= pos) ++j;
+    const int m = seg_start[act_seg[j]] + pos - act_pre[j];
+    in.m = m;
+    in.c = cell[m];
+    in.fx = fxs[m];
+    in.fy = fys[m];
+    if (MODE == 1) {
+        in.yy = y[m];
+        in.vv = v[m];
     }
 }
 
@@ -117,7 +55,7 @@ __device__ __forceinline__ void warp_seg_add(bool ok, int ls, A a, A b, double* 
 // MODE 1 (pd): for visibilities of active blocks r = v + G b - y, with FP64 sums of
 // ||r||^2 and ||G b - y||^2 per (tile, block) segment (per-warp slots, summed in warp order).
 template <typename R, int J, int MODE>
-__global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ grid, cplx_t<R>* __restrict__ out,
+__global__ void __launch_bounds__(256, J <= 8 ? (sizeof(R) == 4 ? 5 : 3) : 1) k_degrid(const cplx_t<R>* __restrict__ grid, cplx_t<R>* __restrict__ out,
                                                 const cplx_t<R>* __restrict__ y, const cplx_t<R>* __restrict__ v,
                                                 cplx_t<R>* __restrict__ rbuf, const int32_t* __restrict__ cell,
                                                 const R* __restrict__ fxs, const R* __restrict__ fys,
@@ -173,17 +111,23 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
         const int nact = nact_s, total = act_pre[nact];
         double* mypart = part + 2 * nseg_t * warp;
         int j = 0;   // segment cursor: positions only grow, so it only moves forward
+        // the inputs of the point blockDim.x positions ahead are loaded while this one is worked on
+        DegridIn<R> nx{};
+        if ((int)threadIdx.x < total) degrid_load<R, MODE>(nx, threadIdx.x, j, act_seg, act_pre, seg_start, cell, fxs, fys, y, v);
         for (int base = 0; base < total; base += blockDim.x) {
             const int pos = base + threadIdx.x;
             const bool ok = pos < total;
+            const DegridIn<R> in = nx;
+            const int jcur = j;
+            if (pos + (int)blockDim.x < total)
+                degrid_load<R, MODE>(nx, pos + blockDim.x, j, act_seg, act_pre, seg_start, cell, fxs, fys, y, v);
             R ar = R(0), ad = R(0);     // squares in the working precision (exact for FP64)
             if (ok) {
-                while (act_pre[j + 1] <= pos) ++j;
-                const int m = seg_start[act_seg[j]] + pos - act_pre[j];
+                const int m = in.m;
                 R wx[J], wy[J];
-                kb_taps<R, J>(fxs[m], wx, two_over_j, beta, kp);
-                kb_taps<R, J>(fys[m], wy, two_over_j, beta, kp);
-                const int c = cell[m];
+                kb_taps<R, J>(in.fx, wx, two_over_j, beta, kp);
+                kb_taps<R, J>(in.fy, wy, two_over_j, beta, kp);
+                const int c = in.c;
                 const int r0 = (c >> 16) - oy, c0 = (c & 0xFFFF) - ox;   // footprint origin in the window
                 R sx = 0, sy = 0;
                 if constexpr (PAIRS) {
@@ -219,15 +163,14 @@ __global__ void __launch_bounds__(256) k_degrid(const cplx_t<R>* __restrict__ gr
                 if (MODE == 0) {
                     oimg[perm[m]] = mk<C2>(sx, sy);
                 } else {
-                    const C2 yy = y[m], vv = v[m];
-                    const R dx = sx - yy.x, dy = sy - yy.y;
-                    const C2 r = mk<C2>(vv.x + dx, vv.y + dy);
+                    const R dx = sx - in.yy.x, dy = sy - in.yy.y;
+                    const C2 r = mk<C2>(in.vv.x + dx, in.vv.y + dy);
                     rbuf[m] = r;
                     ar = r.x * r.x + r.y * r.y;
                     ad = dx * dx + dy * dy;
                 }
             }
-            if (MODE == 1) warp_seg_add(ok, j, ar, ad, mypart);
+            if (MODE == 1) warp_seg_add(ok, jcur, ar, ad, mypart);
         }
         __syncthreads();
         if (MODE == 1) {
@@ -280,49 +223,6 @@ __global__ void k_block_norms(const double* __restrict__ part, const int32_t* __
 }
 
 // ---------------------------------------------------------------- gridding
-// value of visibility m to grid: MODE 0 the input (user order); MODE 1 the dual change
-// v_new - v_old with v_new = scale_i r (step 8), writing v_new.
-template <typename R, int MODE>
-__device__ __forceinline__ cplx_t<R> grid_value(int m, const cplx_t<R>* __restrict__ src,
-                                                const cplx_t<R>* __restrict__ rbuf, cplx_t<R>* __restrict__ v,
-                                                const int32_t* __restrict__ perm, R sc) {
-    if (MODE == 0) return src[perm[m]];
-    const cplx_t<R> r = rbuf[m], vo = v[m];
-    const cplx_t<R> vn = cscale(r, sc);
-    v[m] = vn;
-    return csub(vn, vo);
-}
-
-// U += the tile's E x E window (tile and halo, wrapped periodically), the window's value
-// of cell (ey, ex) given by val(ey, ex). The U reads of a batch of cells go out together.
-template <typename R, class V>
-__device__ __forceinline__ void add_window(cplx_t<R>* __restrict__ U, int oy, int ox, const Geo& g, const V& val) {
-    using C2 = cplx_t<R>;
-    const int E = g.ext, H = g.halo_lo;
-    constexpr int EB = 8;
-    for (int i0 = threadIdx.x; i0 < E * E; i0 += EB * (int)blockDim.x) {
-        C2 uo[EB];
-        int64_t off[EB];
-#pragma unroll
-        for (int k = 0; k < EB; ++k) {
-            const int i = i0 + k * (int)blockDim.x;
-            off[k] = -1;
-            if (i < E * E) {
-                const int ey = i / E, ex = i - ey * E;
-                off[k] = panel_off((oy - H + ey) & (g.Ky - 1), (ox - H + ex) & (g.Kx - 1), g.Ky);
-                uo[k] = U[off[k]];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < EB; ++k) {
-            if (off[k] < 0) break;
-            const int i = i0 + k * (int)blockDim.x;
-            const int ey = i / E, ex = i - ey * E;
-            U[off[k]] = cadd(uo[k], val(ey, ex));
-        }
-    }
-}
-
 // Generic J: one thread per visibility, shared-memory atomics per tap.
 template <typename R, int J, int MODE>
 __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf,
@@ -392,23 +292,41 @@ __global__ void __launch_bounds__(256) k_grid(const cplx_t<R>* __restrict__ src,
 // them to its window when the row changes.
 // Staging (one lane per point, 32 points per chunk) writes per-class records that make
 // the lane's work a fixed-address read: for row class r the weight times the value,
-// phi_y(tap) d; for column class c the pair (weight if the class cell is the low
-// candidate, weight if it is the high one), one of them zero.
+// phi_y(tap) d; for column class c the weight of its tap, negated when the class cell is
+// the high candidate (the weights are positive, so the sign carries the choice and the
+// lane splits it with max(w, 0) and max(-w, 0)). The staging lane rotates its taps into
+// class order in registers (three conditional shifts), so the column record is two
+// aligned 16-byte stores and one 8-byte read per lane and point.
 constexpr int GW_MAXW = 16;    // warps per CTA: one per super-cell column (tile <= 128)
 constexpr int GW_RREC = 9;     // row records per staged point (8, padded against bank conflicts)
-constexpr int GW_CREC = 20;    // column record reals per staged point (16, padded, 16-byte rows)
+constexpr int GW_CREC = 12;    // column record reals per staged point (8, padded: 16-byte rows, no conflicts)
 constexpr int GW_WP = 18;      // window pitch (complex): the 16 columns of one super-cell column's footprints,
                                // padded so that the 8 rows a warp's flush touches start in distinct banks
 
-template <typename R> __device__ __forceinline__ void ld4(const R* p, R& a, R& b, R& c, R& d) {
+template <typename R> __device__ __forceinline__ void ld2r(const R* p, R& a, R& b) {
     if constexpr (sizeof(R) == 4) {
-        const float4 q = *reinterpret_cast<const float4*>(p);
-        a = q.x; b = q.y; c = q.z; d = q.w;
+        const float2 q = *reinterpret_cast<const float2*>(p);
+        a = q.x; b = q.y;
     } else {
-        const double2 q0 = *reinterpret_cast<const double2*>(p), q1 = *reinterpret_cast<const double2*>(p + 2);
-        a = q0.x; b = q0.y; c = q1.x; d = q1.y;
+        const double2 q = *reinterpret_cast<const double2*>(p);
+        a = q.x; b = q.y;
     }
 }
+template <typename R> __device__ __forceinline__ void st4(R* p, R a, R b, R c, R d) {
+    if constexpr (sizeof(R) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+    } else {
+        *reinterpret_cast<double2*>(p) = make_double2(a, b);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
+    }
+}
+// lo, hi += the class weight's low / high part times ry
+template <typename C2, typename R> __device__ __forceinline__ void acc_cand(C2& lo, C2& hi, R w, C2 ry) {
+    const R wl = w > R(0) ? w : R(0), wh = w < R(0) ? -w : R(0);
+    lo.x += wl * ry.x; lo.y += wl * ry.y;
+    hi.x += wh * ry.x; hi.y += wh * ry.y;
+}
+
 // p[0] += a, p[1] += b (two adjacent complex cells, 16-byte aligned in FP32)
 template <typename C2> __device__ __forceinline__ void add2(C2* p, C2 a, C2 b) {
     if constexpr (sizeof(C2) == 8) {
@@ -568,14 +486,26 @@ __global__ void __launch_bounds__(GW_MAXW * 32) k_grid8w(
                     const R wv = b < J ? wy[b] : R(0);
                     rr[(r0 + b) & 7] = mk<C2>(wv * d.x, wv * d.y);
                 }
+                // class c = (gam + a) mod 8 takes tap a = (c - gam) mod 8; its cell is the high
+                // candidate (window column c + 8) when gam + a >= 8, i.e. when c < gam
                 const int gam = c0 & 7;                             // c0 = 8 warp + gam
-                R* cr = crec + lane * GW_CREC;
+                R cw[8];
 #pragma unroll
-                for (int a = 0; a < 8; ++a) {
-                    const R wv = a < J ? wx[a] : R(0);
-                    const int sidx = gam + a;                       // column in the warp's window
-                    *reinterpret_cast<C2*>(cr + 2 * (sidx & 7)) = sidx >= 8 ? mk<C2>(R(0), wv) : mk<C2>(wv, R(0));
+                for (int a = 0; a < 8; ++a) cw[a] = a < J ? wx[a] : R(0);
+#pragma unroll
+                for (int sh = 1; sh < 8; sh <<= 1) {
+                    const bool on = (gam & sh) != 0;
+                    R t[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) t[c] = on ? cw[(c - sh) & 7] : cw[c];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) cw[c] = t[c];
                 }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) cw[c] = c < gam ? -cw[c] : cw[c];
+                R* cr = crec + lane * GW_CREC;
+                st4(cr, cw[0], cw[1], cw[2], cw[3]);
+                st4(cr + 4, cw[4], cw[5], cw[6], cw[7]);
                 mykey = r0;
             }
             // the next chunk's loads go out now and land while this one is accumulated
@@ -593,31 +523,24 @@ __global__ void __launch_bounds__(GW_MAXW * 32) k_grid8w(
                 const int q1 = starts ? __ffs(starts) - 1 : fill;
                 const int r0 = __shfl_sync(0xffffffffu, mykey, q0);
                 // the run's first point starts the running sums, the others add to them two at a time
-                C2 lo0, hi0, lo1, hi1;
-                {
-                    const C2 ry = rrec[q0 * GW_RREC + lcy];
-                    R wl0, wh0, wl1, wh1;
-                    ld4(crec + q0 * GW_CREC + 2 * lcx, wl0, wh0, wl1, wh1);
-                    lo0 = mk<C2>(wl0 * ry.x, wl0 * ry.y); hi0 = mk<C2>(wh0 * ry.x, wh0 * ry.y);
-                    lo1 = mk<C2>(wl1 * ry.x, wl1 * ry.y); hi1 = mk<C2>(wh1 * ry.x, wh1 * ry.y);
-                }
-                int q = q0 + 1;
+                C2 lo0 = mk<C2>(R(0), R(0)), hi0 = lo0, lo1 = lo0, hi1 = lo0;
+                int q = q0;
                 for (; q + 1 < q1; q += 2) {
                     const C2 ra = rrec[q * GW_RREC + lcy], rb = rrec[(q + 1) * GW_RREC + lcy];
-                    R al0, ah0, al1, ah1, bl0, bh0, bl1, bh1;
-                    ld4(crec + q * GW_CREC + 2 * lcx, al0, ah0, al1, ah1);
-                    ld4(crec + (q + 1) * GW_CREC + 2 * lcx, bl0, bh0, bl1, bh1);
-                    lo0.x += al0 * ra.x; lo0.y += al0 * ra.y; hi0.x += ah0 * ra.x; hi0.y += ah0 * ra.y;
-                    lo1.x += al1 * ra.x; lo1.y += al1 * ra.y; hi1.x += ah1 * ra.x; hi1.y += ah1 * ra.y;
-                    lo0.x += bl0 * rb.x; lo0.y += bl0 * rb.y; hi0.x += bh0 * rb.x; hi0.y += bh0 * rb.y;
-                    lo1.x += bl1 * rb.x; lo1.y += bl1 * rb.y; hi1.x += bh1 * rb.x; hi1.y += bh1 * rb.y;
+                    R a0, a1, b0, b1;
+                    ld2r(crec + q * GW_CREC + lcx, a0, a1);
+                    ld2r(crec + (q + 1) * GW_CREC + lcx, b0, b1);
+                    acc_cand(lo0, hi0, a0, ra);
+                    acc_cand(lo1, hi1, a1, ra);
+                    acc_cand(lo0, hi0, b0, rb);
+                    acc_cand(lo1, hi1, b1, rb);
                 }
                 if (q < q1) {
                     const C2 ry = rrec[q * GW_RREC + lcy];
-                    R wl0, wh0, wl1, wh1;
-                    ld4(crec + q * GW_CREC + 2 * lcx, wl0, wh0, wl1, wh1);
-                    lo0.x += wl0 * ry.x; lo0.y += wl0 * ry.y; hi0.x += wh0 * ry.x; hi0.y += wh0 * ry.y;
-                    lo1.x += wl1 * ry.x; lo1.y += wl1 * ry.y; hi1.x += wh1 * ry.x; hi1.y += wh1 * ry.y;
+                    R a0, a1;
+                    ld2r(crec + q * GW_CREC + lcx, a0, a1);
+                    acc_cand(lo0, hi0, a0, ry);
+                    acc_cand(lo1, hi1, a1, ry);
                 }
                 C2* cp = win + (r0 + ((lcy - r0) & 7)) * GW_WP + lcx;
                 add2(cp, lo0, lo1);
@@ -640,23 +563,13 @@ __global__ void __launch_bounds__(GW_MAXW * 32) k_grid8w(
 }
 
 // ---------------------------------------------------------------- launchers
-#define PD_J_DISPATCH(J_, CALL)                          \
-    switch (J_) {                                        \
-        case 2: { constexpr int JJ = 2; CALL; } break;   \
-        case 4: { constexpr int JJ = 4; CALL; } break;   \
-        case 6: { constexpr int JJ = 6; CALL; } break;   \
-        case 8: { constexpr int JJ = 8; CALL; } break;   \
-        case 10: { constexpr int JJ = 10; CALL; } break; \
-        case 12: { constexpr int JJ = 12; CALL; } break; \
-        case 14: { constexpr int JJ = 14; CALL; } break; \
-        case 16: { constexpr int JJ = 16; CALL; } break; \
-        default: return cudaErrorInvalidValue;           \
-    }
 
 template <typename R, int J, int MODE>
 static cudaError_t launch_degrid(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out, const DualArgs* a,
                                  const int32_t* tiles, const int32_t* count, int ctas, cudaStream_t s,
                                  int batch = 1) {
+    if constexpr (J <= 8)
+        if (p->g_mode == PD_G_CSR) return launch_degrid_csr<R, J, MODE>(p, grid, out, a, tiles, count, ctas, s, batch);
     const Geo& g = p->g;
     const int ms = std::max(p->max_tile_segs, 1);
     const size_t win = sizeof(R) == 4 ? (size_t)2 * g.ext * ((g.ext + 2) & ~1) : (size_t)g.ext * g.ext;
@@ -723,6 +636,8 @@ cudaError_t degrid_res_norms(const pd_plan* p, const cplx_t<R>* grid, const cplx
 template <typename R, int J, int MODE>
 static cudaError_t launch_grid_j(const pd_plan* p, const cplx_t<R>* src, const DualArgs* a, const int32_t* tiles,
                                  const int32_t* count, cplx_t<R>* U, int* next_tile, cudaStream_t s, int batch) {
+    if constexpr (J <= 8)
+        if (p->g_mode == PD_G_CSR) return launch_grid_csr<R, J, MODE>(p, src, a, tiles, count, U, next_tile, s, batch);
     const Geo& g = p->g;
     const int ms = std::max(p->max_tile_segs, 1);
     const size_t lists = (size_t)(2 * ms + 1) * sizeof(int);

@@ -73,6 +73,9 @@ struct pd_plan {
     void* fx = nullptr;            // real [M]: fractional part of g_x
     void* fy = nullptr;
     int32_t* perm = nullptr;       // internal -> user index
+    int g_mode = PD_G_ON_THE_FLY;  // PD_G_CSR: G stored explicitly, below
+    int32_t* csr_col = nullptr;    // [J^2][M] grid cell (ky << 16 | kx) of each entry, internal order
+    void* csr_val = nullptr;       // real [J^2][M] weight of each entry
     int32_t* seg_start = nullptr;  // [nseg + 1]
     int32_t* seg_block = nullptr;  // [nseg]
     int32_t* tile_seg_start = nullptr;  // [ntiles + 1]
@@ -224,6 +227,8 @@ cudaError_t degrid_res_norms(const pd_plan* p, const cplx_t<R>* grid, const cplx
 template <typename R>
 cudaError_t degrid_dual(const pd_plan* p, const cplx_t<R>* grid, const DualArgs& a, const int32_t* tiles,
                         const int32_t* counts, cudaStream_t s);
+// G in CSR form (PD_G_CSR): the J^2 (cell, weight) entries of every visibility
+cudaError_t build_csr(pd_plan* p, cudaStream_t s);
 // plain grid: U = G^T y_user (U overwritten) for `batch` inputs (stride M) and grids (stride Kx Ky)
 template <typename R>
 cudaError_t grid_plain(const pd_plan* p, const cplx_t<R>* y_user, cplx_t<R>* U, cudaStream_t s, int batch = 1);
@@ -243,7 +248,10 @@ cudaError_t psi_plain(const pd_plan* p, const R* coeffs, R* x, cudaStream_t s);
 // pd: for active bases s <- clip(s + Psi_j^H x~ / sqrt(b), -alpha, alpha); s~ += Psi (s_new - s_old)
 template <typename R>
 cudaError_t sparsity_dual(const pd_plan* p, const R* xt, R* s, R* st, const int32_t* basis_active,
-                          double alpha, cudaStream_t s_);
+                          double alpha, cudaStream_t s_, const R* wt = nullptr);
+// weights of the reweighted prior: w = delta / (delta + |Psi^H x|), w real [b][ny][nx]
+template <typename R>
+cudaError_t sara_weights(const pd_plan* p, const R* x, double delta, R* w, cudaStream_t s);
 
 // ---- pd_kernels.cu
 struct SelectArgs {

@@ -65,7 +65,8 @@ constexpr int ARB = 4;   // analysis outputs per thread along a row (row pass) o
 // step-13 update of s and its change ds.
 template <typename R, int MODE, int LF>
 __device__ __forceinline__ void dwt_body(const R* __restrict__ src, R* __restrict__ ll_out, R* __restrict__ out,
-                                         R* __restrict__ ds, const R* __restrict__ filt, int k, int my, int mx,
+                                         R* __restrict__ ds, const R* __restrict__ wt, const R* __restrict__ filt,
+                                         int k, int my, int mx,
                                          int oy0, int ox0, int ty, int tx, bool last, int64_t boff, int nx,
                                          int64_t ll_off, R scale, R alpha, R* sm) {
     constexpr int NX = LF + 2 * ARB - 2;               // staged values per ARB outputs
@@ -138,11 +139,12 @@ __device__ __forceinline__ void dwt_body(const R* __restrict__ src, R* __restric
                     if (store_lo) out[p_lo] = lo * scale;
                     out[p_hi] = hi * scale;
                 } else {
+                    // weighted prior: the threshold of each coefficient is alpha times its weight
                     if (store_lo) {
-                        const R so = sold[o][0], sn = clip(so + lo * scale, alpha);
+                        const R so = sold[o][0], sn = clip(so + lo * scale, wt ? alpha * wt[p_lo] : alpha);
                         out[p_lo] = sn; ds[p_lo] = sn - so;
                     }
-                    const R so = sold[o][1], sn = clip(so + hi * scale, alpha);
+                    const R so = sold[o][1], sn = clip(so + hi * scale, wt ? alpha * wt[p_hi] : alpha);
                     out[p_hi] = sn; ds[p_hi] = sn - so;
                 }
                 if (!half && !last) ll_out[ll_off + (int64_t)oy * hx + ox] = lo;
@@ -152,10 +154,12 @@ __device__ __forceinline__ void dwt_body(const R* __restrict__ src, R* __restric
 }
 
 // One level for every basis in blockIdx.z. MODE 0: out = coefficient * scale.
-// MODE 1: s/ds update of step 13. The last level also treats the approximation band.
+// MODE 1: s/ds update of step 13 (wt: per-coefficient weights of the reweighted prior,
+// same layout as s, or null). The last level also treats the approximation band.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(NT_W, 3) k_dwt_level(const R* __restrict__ x0, const R* __restrict__ ll_in,
                                                     R* __restrict__ ll_out, R* __restrict__ out, R* __restrict__ ds,
+                                                    const R* __restrict__ wt,
                                                     const R* __restrict__ filt, const int32_t* __restrict__ flen,
                                                     const int32_t* __restrict__ active, int level, int L, int ny,
                                                     int nx, R scale, R alpha) {
@@ -173,24 +177,25 @@ __global__ void __launch_bounds__(NT_W, 3) k_dwt_level(const R* __restrict__ x0,
     const int64_t boff = (int64_t)k * ny * nx, ll_off = (int64_t)k * (ny / 2) * (nx / 2);
     const bool last = level == L - 1;
     R* sm = reinterpret_cast<R*>(smraw);
-    PD_LF_DISPATCH(lf, (dwt_body<R, MODE, LF>(src, ll_out, out, ds, filt, k, my, mx, oy0, ox0, ty, tx, last, boff,
+    PD_LF_DISPATCH(lf, (dwt_body<R, MODE, LF>(src, ll_out, out, ds, wt, filt, k, my, mx, oy0, ox0, ty, tx, last, boff,
                                               nx, ll_off, scale, alpha, sm)));
 }
 
 // Dirac basis (identity): MODE 0 copies x * scale, MODE 1 applies step 13 elementwise.
 template <typename R, int MODE>
 __global__ void k_dirac(const R* __restrict__ x, R* __restrict__ out, R* __restrict__ ds,
-                        const int32_t* __restrict__ flen, const int32_t* __restrict__ active, int b, int64_t n,
-                        R scale, R alpha) {
+                        const R* __restrict__ wt, const int32_t* __restrict__ flen,
+                        const int32_t* __restrict__ active, int b, int64_t n, R scale, R alpha) {
     for (int k = 0; k < b; ++k) {
         if (flen[k] != 0 || (MODE == 1 && !active[k])) continue;
         R* o = out + (int64_t)k * n;
         R* d = ds + (int64_t)k * n;
+        const R* wk = wt ? wt + (int64_t)k * n : nullptr;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
             if (MODE == 0) {
                 o[i] = x[i] * scale;
             } else {
-                const R so = o[i], sn = clip(so + x[i] * scale, alpha);
+                const R so = o[i], sn = clip(so + x[i] * scale, wk ? alpha * wk[i] : alpha);
                 o[i] = sn;
                 d[i] = sn - so;
             }
@@ -397,16 +402,16 @@ template <typename R> static size_t syn_smem(int ty, int tx) {
 
 template <typename R>
 static cudaError_t analysis(const pd_plan* p, const R* x, R* out, R* ds, const int32_t* active, int mode, R alpha,
-                            cudaStream_t s) {
+                            cudaStream_t s, const R* wt = nullptr) {
     cudaError_t e;
     const int ny = p->g.ny, nx = p->g.nx, b = p->b, L = p->L;
     const R scale = R(1.0 / std::sqrt((double)b));
     const int64_t n = (int64_t)ny * nx;
     int dgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)p->num_sms * 4);
     if (mode == 0)
-        k_dirac<R, 0><<<dgrid, 256, 0, s>>>(x, out, out, p->filt_len, active, b, n, scale, alpha);
+        k_dirac<R, 0><<<dgrid, 256, 0, s>>>(x, out, out, nullptr, p->filt_len, active, b, n, scale, alpha);
     else
-        k_dirac<R, 1><<<dgrid, 256, 0, s>>>(x, out, ds, p->filt_len, active, b, n, scale, alpha);
+        k_dirac<R, 1><<<dgrid, 256, 0, s>>>(x, out, ds, wt, p->filt_len, active, b, n, scale, alpha);
     if ((e = cudaGetLastError())) return e;
     if (p->n_wavelet == 0) return cudaSuccess;
     for (int lev = 0; lev < L; ++lev) {
@@ -418,11 +423,11 @@ static cudaError_t analysis(const pd_plan* p, const R* x, R* out, R* ds, const i
         const size_t sm = ana_smem<R>(ty, tx);
         if ((e = ensure_smem(k_dwt_level<R, 0>, sm)) || (e = ensure_smem(k_dwt_level<R, 1>, sm))) return e;
         if (mode == 0)
-            k_dwt_level<R, 0><<<grid, NT_W, sm, s>>>(x, llin, llout, out, nullptr, (const R*)p->filt, p->filt_len,
-                                                     active, lev, L, ny, nx, scale, alpha);
+            k_dwt_level<R, 0><<<grid, NT_W, sm, s>>>(x, llin, llout, out, nullptr, nullptr, (const R*)p->filt,
+                                                     p->filt_len, active, lev, L, ny, nx, scale, alpha);
         else
-            k_dwt_level<R, 1><<<grid, NT_W, sm, s>>>(x, llin, llout, out, ds, (const R*)p->filt, p->filt_len, active,
-                                                     lev, L, ny, nx, scale, alpha);
+            k_dwt_level<R, 1><<<grid, NT_W, sm, s>>>(x, llin, llout, out, ds, wt, (const R*)p->filt, p->filt_len,
+                                                     active, lev, L, ny, nx, scale, alpha);
         if ((e = cudaGetLastError())) return e;
     }
     return cudaSuccess;
@@ -468,11 +473,28 @@ cudaError_t psi_plain(const pd_plan* p, const R* coeffs, R* x, cudaStream_t s) {
     return synthesis<R>(p, coeffs, x, p->ones_basis, 0, s);
 }
 
+// w = delta / (delta + |w|) in place (the reweighting rule of the weighted analysis prior)
+template <typename R>
+__global__ void k_sara_rule(R* __restrict__ w, int64_t n, R delta) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = delta / (delta + fabs(w[i]));
+}
+
+template <typename R>
+cudaError_t sara_weights(const pd_plan* p, const R* x, double delta, R* w, cudaStream_t s) {
+    cudaError_t e = psi_adj_plain<R>(p, x, w, s);
+    if (e) return e;
+    const int64_t n = (int64_t)p->b * p->g.ny * p->g.nx;
+    const int ctas = (int)std::min<int64_t>((n + 255) / 256, (int64_t)p->num_sms * 8);
+    k_sara_rule<R><<<ctas, 256, 0, s>>>(w, n, (R)delta);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t sparsity_dual(const pd_plan* p, const R* xt, R* s, R* st, const int32_t* basis_active, double alpha,
-                          cudaStream_t str) {
+                          cudaStream_t str, const R* wt) {
     prof_mark(PH_ANALYSIS, 0, str);
-    cudaError_t e = analysis<R>(p, xt, s, (R*)p->ds, basis_active, 1, (R)alpha, str);
+    cudaError_t e = analysis<R>(p, xt, s, (R*)p->ds, basis_active, 1, (R)alpha, str, wt);
     prof_mark(PH_ANALYSIS, 1, str);
     if (e) return e;
     prof_mark(PH_SYNTHESIS, 0, str);
@@ -579,7 +601,7 @@ static pd_status psi_adj_static_t(const R* x, R* coeffs, int nx, int ny, int L, 
     const R scale = R(1.0 / std::sqrt((double)b));
     const int64_t n = (int64_t)ny * nx;
     const int dgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 4);
-    k_dirac<R, 0><<<dgrid, 256, 0, s>>>(x, coeffs, coeffs, flen, ones, b, n, scale, R(0));
+    k_dirac<R, 0><<<dgrid, 256, 0, s>>>(x, coeffs, coeffs, nullptr, flen, ones, b, n, scale, R(0));
     if ((e = cudaGetLastError())) return set_error(PD_ECUDA, cudaGetErrorString(e));
     if (nwav == 0) return PD_OK;
     for (int lev = 0; lev < L; ++lev) {
@@ -588,8 +610,8 @@ static pd_status psi_adj_static_t(const R* x, R* coeffs, int nx, int ny, int L, 
         dim3 grid((hx + tx - 1) / tx, (hy + ty - 1) / ty, b);
         const size_t sm = ana_smem<R>(ty, tx);
         if ((e = ensure_smem(k_dwt_level<R, 0>, sm))) return set_error(PD_ECUDA, cudaGetErrorString(e));
-        k_dwt_level<R, 0><<<grid, NT_W, sm, s>>>(x, ll[(lev + 1) & 1], ll[lev & 1], coeffs, nullptr, filt, flen, ones,
-                                                 lev, L, ny, nx, scale, R(0));
+        k_dwt_level<R, 0><<<grid, NT_W, sm, s>>>(x, ll[(lev + 1) & 1], ll[lev & 1], coeffs, nullptr, nullptr, filt,
+                                                 flen, ones, lev, L, ny, nx, scale, R(0));
         if ((e = cudaGetLastError())) return set_error(PD_ECUDA, cudaGetErrorString(e));
     }
     return PD_OK;
@@ -653,8 +675,10 @@ template cudaError_t psi_adj_plain<double>(const pd_plan*, const double*, double
 template cudaError_t psi_plain<float>(const pd_plan*, const float*, float*, cudaStream_t);
 template cudaError_t psi_plain<double>(const pd_plan*, const double*, double*, cudaStream_t);
 template cudaError_t sparsity_dual<float>(const pd_plan*, const float*, float*, float*, const int32_t*, double,
-                                          cudaStream_t);
+                                          cudaStream_t, const float*);
 template cudaError_t sparsity_dual<double>(const pd_plan*, const double*, double*, double*, const int32_t*, double,
-                                           cudaStream_t);
+                                           cudaStream_t, const double*);
+template cudaError_t sara_weights<float>(const pd_plan*, const float*, double, float*, cudaStream_t);
+template cudaError_t sara_weights<double>(const pd_plan*, const double*, double, double*, cudaStream_t);
 
 }  // namespace pdgb

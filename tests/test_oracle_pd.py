@@ -45,15 +45,18 @@ def test_power_method_matches_dense_eigenvalue():
     assert psi2 == pytest.approx(1.0, rel=1e-12)
 
 
-def admm_reference(prob, iters=30000, rho=1.0):
+def admm_reference(prob, iters=30000, rho=1.0, weights=None):
     """Independent solver of problem (basic-min-problem) on dense matrices.
 
     ADMM on min ||W x||_1 + i_{x>=0}(x) + sum_i i_{B_i}(A_i x) with the splitting
     z = K x, K = [W; I; A_1; ...; A_d]; the x-step is a dense linear solve.
+    weights: per-coefficient weights of the reweighted prior (W = diag(w) Psi^H).
     """
     g = prob.geom
     N = g.ny * g.nx
     W = np.array([prob.psi_adj(e.reshape(g.ny, g.nx)).ravel() for e in np.eye(N)]).T
+    if weights is not None:
+        W = np.asarray(weights).ravel()[:, None] * W
     A = dense_phi(prob)
     M = len(prob.uv)
     rows = []
