@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(PassShape<R, N>::NT_COLS, PassShape<R, N>::MIN
     const int p = blockIdx.x / PER, q0 = (blockIdx.x % PER) * CQ;
     const C2* src = t1 + (int64_t)p * N * 4 + q0;
     struct In { C2 val, w; };
-    batched_loop<4, NT>(N * CQ, [&](int e) {
+    batched_loop<8, NT>(N * CQ, [&](int e) {
         const int iy = e / CQ, qq = e % CQ;
         return In{src[iy * 4 + qq], __ldg(&twy[(iy - N / 2) & (Ky - 1)])};
     }, [&](int e, const In& v) {
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(PassShape<R, N>::NT_COLS, PassShape<R, N>::MIN
     constexpr int NT = P::NT_COLS, CQ = P::CQ, Ky = 2 * N, PER = 4 / CQ;
     const int p = blockIdx.x / PER, q0 = (blockIdx.x % PER) * CQ;
     struct In { C2 u, um; };
-    batched_loop<4, NT>(Ky * CQ, [&](int e) {
+    batched_loop<8, NT>(Ky * CQ, [&](int e) {
         const int ky = e / CQ, qq = e % CQ;
         const int kx = 4 * p + q0 + qq;
         const int mkx = (Kx - kx) & (Kx - 1), mky = (Ky - ky) & (Ky - 1);
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(PassShape<R, N>::NT_ROWS, PassShape<R, N>::MIN
     constexpr int NT = P::NT_ROWS, Kx = 2 * N, NPH = N / 4 + 1;
     const int iy0 = blockIdx.x * 2 * P::PAIRS;
     struct In { C2 ta, tb; };
-    batched_loop<4, NT>(NPH * P::PAIRS * 4, [&](int e) {
+    batched_loop<8, NT>(NPH * P::PAIRS * 4, [&](int e) {
         const int q = e & 3, pr = (e >> 2) % P::PAIRS, pp = (e >> 2) / P::PAIRS;
         const int a = iy0 + 2 * pr;
         In v;
