@@ -145,7 +145,7 @@ class Clocks:
 
 
 # committed ncu summaries with the measured DRAM traffic of a kernel, per bench phase
-PROFILE_OF_PHASE = {"grid_dual": "k_grid8c_gridding_c5.md", "degrid_dual": "k_degrid_degridding_c5.md"}
+PROFILE_OF_PHASE = {"grid_dual": "k_grid8w_gridding_c5.md", "degrid_dual": "k_degrid_degridding_c5.md"}
 
 
 def kernel_source_hash(path, name):
@@ -154,8 +154,15 @@ def kernel_source_hash(path, name):
     import hashlib
     import re
     text = open(path).read()
-    m = re.search(r"__global__ void(?:\s+__launch_bounds__\([^)]*\))?\s+" + re.escape(name) + r"\(", text)
-    if not m:
+    start = None
+    for m in re.finditer(r"\b" + re.escape(name) + r"\(", text):
+        # the declaration this name opens: text since the previous statement or block end
+        lo = max(text.rfind(";", 0, m.start()), text.rfind("}", 0, m.start())) + 1
+        g = text.find("__global__", lo, m.start())
+        if g >= 0:
+            start = g
+            break
+    if start is None:
         return None
     depth = 0
     for j in range(text.index("{", m.end()), len(text)):
@@ -164,7 +171,7 @@ def kernel_source_hash(path, name):
         elif text[j] == "}":
             depth -= 1
             if depth == 0:
-                return hashlib.sha256(text[m.start():j + 1].encode()).hexdigest()
+                return hashlib.sha256(text[start:j + 1].encode()).hexdigest()
     return None
 
 

@@ -83,8 +83,16 @@ def test_plan_descriptions_are_refused_before_any_device_work(lib):
         (dict(levels=7, nx=16, ny=16), 1, b"levels"),
         (dict(tile=4), 1, b"tile"),
         (dict(precision=7), 1, b"precision"),
+        (dict(g_mode=2), 1, b"g_mode"),
+        (dict(g_mode=B.PD_G_CSR, kernel_width=10), 6, b"CSR"),
     ]
     for over, status, text in cases:
         st, msg = create(**over)
         assert st == status, (over, st, msg)
         assert text in msg, (over, msg)
+
+
+def test_reweighting_rule_refuses_bad_arguments_without_gpu(lib):
+    x = np.zeros(4)
+    assert lib.pd_sara_weights(None, x.ctypes.data, ctypes.c_double(0.1), x.ctypes.data, None) == 1
+    assert b"pd_sara_weights" in lib.pd_last_error()

@@ -29,7 +29,9 @@ def test_traffic_dropped_once_the_kernel_source_changes(tmp_path, monkeypatch):
         f.write("\n// an edit elsewhere in the file keeps the kernel's counters\n")
     assert bench.measured_traffic("grid_dual", "c5") == orig
     text = (tmp_path / src_rel).read_text()
-    (tmp_path / src_rel).write_text(text.replace("const int pk = scl[warp][q];", "const int pk = scl[warp][q] + 0;"))
+    edited = text.replace("const int gam = c0 & 7;", "const int gam = (c0 & 7) + 0;")
+    assert edited != text
+    (tmp_path / src_rel).write_text(edited)
     assert bench.measured_traffic("grid_dual", "c5") is None
     if orig is not None:       # the copy matched its recorded hash before the edit
         assert orig > 0
