@@ -270,9 +270,10 @@ typedef struct {
                                       degridding pass over all visibilities per iteration) */
     int32_t per_block;             /* 1: the plain per-block form, for comparison with the batched
                                       one: the host draws the active sets (same Philox draws) and
-                                      launches the degridding, ball projection, gridding and halo
-                                      merge once per active block and the wavelet analysis and
-                                      synthesis once per active basis; same results up to rounding
+                                      launches the degridding, ball projection and gridding
+                                      (four tile-colour launches) once per active block and the
+                                      wavelet analysis and synthesis once per active basis;
+                                      same results up to rounding
                                       order. Needs adaptive = 0 and use_graph = 0; synchronises
                                       `stream` after every iteration. */
     const void* sparsity_weights;  /* NULL: the l1 prior of Sec. 2 (problem analysis-l1). Else device
@@ -321,7 +322,7 @@ pd_status pd_state_u(pd_state* st, void** u, int64_t* elements);
 /*
  * Per-phase kernel times accumulated by iterations run with params.profile = 1:
  * ms[k] (host) is the summed CUDA-event time of phase k and iterations[k] how
- * many iterations contributed, for k < min(n, 12); reset = 1 clears the sums.
+ * many iterations contributed, for k < min(n, 11); reset = 1 clears the sums.
  * Phase names come from pd_phase_name(k) (e.g. "degrid_dual", "fwd_cols").
  */
 pd_status pd_state_profile(pd_state* st, double* ms, int64_t* iterations, int32_t n, int32_t reset);

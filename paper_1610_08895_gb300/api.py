@@ -34,6 +34,9 @@ def _need(t, dtype, shape, name):
         raise ValueError(f"{name} must be contiguous")
 
 
+# kernel phases timed by pd_iterate(profile=True) (pd_phase_name 0 .. N_PHASES - 1)
+N_PHASES = 11
+
 _G_MODE = {"on_the_fly": B.PD_G_ON_THE_FLY, "csr": B.PD_G_CSR}
 
 
@@ -260,11 +263,11 @@ class State:
 
     def profile(self, reset=False):
         """{phase name: (total ms, iterations)} from iterations run with profile=True."""
-        ms = np.zeros(12)
-        n = np.zeros(12, dtype=np.int64)
-        B.call("pd_state_profile", self._h, ms.ctypes.data, n.ctypes.data, 12, int(bool(reset)))
+        ms = np.zeros(N_PHASES)
+        n = np.zeros(N_PHASES, dtype=np.int64)
+        B.call("pd_state_profile", self._h, ms.ctypes.data, n.ctypes.data, N_PHASES, int(bool(reset)))
         lib = B.load()
-        return {lib.pd_phase_name(k).decode(): (float(ms[k]), int(n[k])) for k in range(12)}
+        return {lib.pd_phase_name(k).decode(): (float(ms[k]), int(n[k])) for k in range(N_PHASES)}
 
     def save(self):
         p = self.plan

@@ -39,7 +39,7 @@ void pdgb::prof_mark(int phase, int end, cudaStream_t s) {
 }
 
 static const char* k_phase_names[PH_COUNT] = {
-    "select", "fwd_rows", "fwd_cols", "degrid_dual", "block_norms", "grid_dual", "halo_merge",
+    "select", "fwd_rows", "fwd_cols", "degrid_dual", "block_norms", "grid_dual",
     "wavelet_analysis", "wavelet_synthesis", "inv_cols", "inv_rows_primal", "primal_finish"};
 
 extern "C" const char* pd_phase_name(int32_t phase) {

@@ -180,7 +180,7 @@ namespace pdgb {
 
 // Kernel phases of one iteration, for optional per-phase CUDA-event timing.
 enum Phase {
-    PH_SELECT = 0, PH_FWD_ROWS, PH_FWD_COLS, PH_DEGRID, PH_NORMS, PH_GRID, PH_HALO, PH_ANALYSIS,
+    PH_SELECT = 0, PH_FWD_ROWS, PH_FWD_COLS, PH_DEGRID, PH_NORMS, PH_GRID, PH_ANALYSIS,
     PH_SYNTHESIS, PH_INV_COLS, PH_INV_ROWS, PH_FINISH, PH_COUNT
 };
 // Record the start (end = 0) or end (end = 1) event of a phase on stream s when the
