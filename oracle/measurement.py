@@ -153,6 +153,37 @@ class Geometry:
                 im += np.bincount(idx, weights=w * vis.imag, minlength=size)
         return (re + 1j * im).reshape(self.Ky, self.Kx)
 
+    # --- G with direction-dependent effects (DDEs) ---------------------------
+    # Sec. 2: the sparse G "models the compact support DDEs as a convolution in the
+    # Fourier domain" on top of the interpolation. Row m of the DDE-aware G is the J x J
+    # interpolation kernel of point m convolved with that point's d x d Fourier-domain
+    # DDE kernel D_m (d odd, offsets -h .. h with h = (d - 1)/2, [ky offset][kx offset]):
+    #   (G b)_m = sum_k D_m[k] sum_c phi_m(c - k) b[c] = sum_k D_m[k] (G (b shifted by -k))_m,
+    # written below as that sum of d^2 plain interpolations of the shifted grid.
+    def degrid_dde(self, grid, uv, dde):
+        """G b with DDE-aware rows: dde is complex [M][d][d] (Sec. 2)."""
+        dde = np.asarray(dde, dtype=np.complex128)
+        d = dde.shape[1]
+        h = (d - 1) // 2
+        out = np.zeros(len(uv), dtype=np.complex128)
+        for i in range(d):
+            for j in range(d):
+                shifted = np.roll(grid, (-(i - h), -(j - h)), axis=(0, 1))   # shifted[c] = grid[c + k]
+                out += dde[:, i, j] * self.degrid(shifted, uv)
+        return out
+
+    def grid_dde(self, vis, uv, dde):
+        """G^H v for the DDE-aware G: the adjoint of each term of degrid_dde."""
+        dde = np.asarray(dde, dtype=np.complex128)
+        vis = np.asarray(vis, dtype=np.complex128)
+        d = dde.shape[1]
+        h = (d - 1) // 2
+        out = np.zeros((self.Ky, self.Kx), dtype=np.complex128)
+        for i in range(d):
+            for j in range(d):
+                out += np.roll(self.grid(np.conj(dde[:, i, j]) * vis, uv), (i - h, j - h), axis=(0, 1))
+        return out
+
     # --- Phi and its real adjoint -----------------------------------------
     def phi(self, x, uv):
         """Phi x = G F Z x for a real image x (Sec. 2)."""

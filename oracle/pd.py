@@ -38,8 +38,10 @@ from . import wavelets as _wav
 class Problem:
     """Data of problem (basic-min-problem): geometry, uv, blocks, Psi, y, epsilon."""
 
-    def __init__(self, geom, uv, block_of_vis, nblocks, basis_ids, levels, y=None, eps=None):
+    def __init__(self, geom, uv, block_of_vis, nblocks, basis_ids, levels, y=None, eps=None, dde=None):
         self.geom = geom
+        # optional Fourier-domain DDE kernels [M][d][d] of the DDE-aware G (Sec. 2)
+        self.dde = None if dde is None else np.asarray(dde, dtype=np.complex128)
         self.uv = np.asarray(uv, dtype=np.float64)
         self.block_of_vis = np.asarray(block_of_vis, dtype=np.int64)
         self.nblocks = int(nblocks)
@@ -49,12 +51,25 @@ class Problem:
         self.y = None if y is None else np.asarray(y, dtype=np.complex128)
         self.eps = None if eps is None else np.asarray(eps, dtype=np.float64)
 
+    # G restricted to the visibilities ix (G_i of eq. data-split), and G^H of all of them
+    def degrid_rows(self, grid, ix):
+        if self.dde is None:
+            return self.geom.degrid(grid, self.uv[ix])
+        return self.geom.degrid_dde(grid, self.uv[ix], self.dde[ix])
+
+    def grid_all(self, v):
+        if self.dde is None:
+            return self.geom.grid(v, self.uv)
+        return self.geom.grid_dde(v, self.uv, self.dde)
+
     # operators of the split problem (eq. data-split)
     def phi(self, x):
-        return self.geom.phi(x, self.uv)
+        g = self.geom
+        return self.degrid_rows(g.fft(g.zpad(x)), np.arange(len(self.uv)))
 
     def phi_adj(self, y):
-        return self.geom.phi_adj(y, self.uv)
+        g = self.geom
+        return np.real(g.zpad_adj(g.fft_adj(self.grid_all(y))))
 
     def psi_adj(self, x):
         return _wav.psi_adj(x, self.basis_ids, self.levels)
@@ -126,7 +141,7 @@ def pd_iteration(problem, st, tau, sigma, varsigma, kappa, psi_norm, seed,
         if not active[i]:
             continue
         ix = problem.block_index[i]
-        gb = problem.geom.degrid(b_tilde, problem.uv[ix])                      # G_i M_i b~
+        gb = problem.degrid_rows(b_tilde, ix)                                  # G_i M_i b~
         st.res_norm[i] = np.linalg.norm(gb - problem.y[ix])
         st.v[ix] = _prox.dual_data_update(st.v[ix], gb, problem.y[ix], problem.eps[i])   # step 8
     # step 13 for the active sparsity bases
@@ -140,7 +155,7 @@ def pd_iteration(problem, st, tau, sigma, varsigma, kappa, psi_norm, seed,
     # step 14: s~ = Psi s
     s_tilde = problem.psi(st.s)
     # step 9 / 17: sum_i M_i^T v~_i = G^T v, then Z^T F^H
-    back = np.real(problem.geom.zpad_adj(problem.geom.fft_adj(problem.geom.grid(st.v, problem.uv))))
+    back = np.real(problem.geom.zpad_adj(problem.geom.fft_adj(problem.grid_all(st.v))))
     # step 17: primal update with the positivity projection
     x_new = _prox.proj_positive(st.x - tau * (sigma * s_tilde + varsigma * back))
     # step 18: over-relaxation
