@@ -83,6 +83,18 @@ typedef struct pd_state pd_state;
  *               J^2 (4 + sizeof real) bytes per visibility (8.6 GB at 16.8M
  *               visibilities, J = 8, FP32), held by the plan. Both modes apply the
  *               same operator (to rounding); CSR needs J <= 8 (PD_ENOTSUP otherwise).
+ * dde_width     0 (or 1 with unit kernels): no direction-dependent effects. Otherwise
+ *               the odd width d >= 3 of each visibility's Fourier-domain DDE kernel,
+ *               and G is the DDE-aware matrix of Sec. 2 (G "models the compact support
+ *               DDEs as a convolution in the Fourier domain"): row m is the J x J
+ *               interpolation kernel convolved with the d x d kernel D_m, so it has
+ *               (J + d - 1)^2 complex entries, (G b)_m = sum_k D_m[k] sum_c
+ *               phi_m(c - k) b[c]. Needs g_mode = PD_G_CSR and J + d - 1 <= 8
+ *               (PD_EINVAL / PD_ENOTSUP otherwise); the entries are complex, so the
+ *               matrix takes (J + d - 1)^2 (4 + 2 sizeof real) bytes per visibility.
+ * dde_kernels   with dde_width >= 3: host complex128 [nvis][d][d] (interleaved re, im),
+ *               user visibility order, D_m[i][j] at grid offset (ky, kx) = (i - h, j - h),
+ *               h = (d - 1) / 2; read during pd_plan_create only.
  */
 typedef struct {
     int32_t nx, ny;
@@ -99,6 +111,8 @@ typedef struct {
     int32_t precision;
     int32_t tile;
     int32_t g_mode;
+    int32_t dde_width;
+    const double* dde_kernels;
 } pd_plan_desc;
 
 typedef enum { PD_G_ON_THE_FLY = 0, PD_G_CSR = 1 } pd_g_mode;

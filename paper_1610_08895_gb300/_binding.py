@@ -33,7 +33,7 @@ class PdPlanDesc(ctypes.Structure):
                 ("block_of_vis", ctypes.c_void_p), ("kernel_width", ctypes.c_int32),
                 ("kb_beta", ctypes.c_double), ("nbases", ctypes.c_int32), ("basis_ids", ctypes.c_void_p),
                 ("levels", ctypes.c_int32), ("precision", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("g_mode", ctypes.c_int32)]
+                ("g_mode", ctypes.c_int32), ("dde_width", ctypes.c_int32), ("dde_kernels", ctypes.c_void_p)]
 
 
 class PdParams(ctypes.Structure):

@@ -45,10 +45,12 @@ class Plan:
 
     g_mode "on_the_fly" evaluates the Kaiser-Bessel weights of G in the kernels; "csr"
     builds G once as a sparse matrix on the device (J^2 column/weight pairs per
-    visibility, J <= 8) and reads it in every application."""
+    visibility, J <= 8) and reads it in every application. dde_kernels (with "csr"):
+    complex [nvis, d, d] Fourier-domain DDE kernels, d odd, user order; G's row m is
+    then the interpolation kernel convolved with kernel m (J + d - 1 <= 8)."""
 
     def __init__(self, nx, ny, uv, block_of_vis, nblocks, kernel_width=8, basis_ids=(0,), levels=1,
-                 precision="f32", tile=0, kb_beta=0.0, g_mode="on_the_fly"):
+                 precision="f32", tile=0, kb_beta=0.0, g_mode="on_the_fly", dde_kernels=None):
         B.load()
         self.nx, self.ny = int(nx), int(ny)
         self.uv = np.ascontiguousarray(uv, dtype=np.float64)
@@ -64,11 +66,17 @@ class Plan:
         if g_mode not in _G_MODE:
             raise ValueError(f"g_mode must be one of {sorted(_G_MODE)}, got {g_mode!r}")
         self.g_mode = g_mode
+        dde_w, dde_ptr = 0, None
+        if dde_kernels is not None:
+            self.dde = np.ascontiguousarray(dde_kernels, dtype=np.complex128)
+            if self.dde.ndim != 3 or self.dde.shape[0] != self.nvis or self.dde.shape[1] != self.dde.shape[2]:
+                raise ValueError(f"dde_kernels must have shape (nvis, d, d), got {self.dde.shape}")
+            dde_w, dde_ptr = self.dde.shape[1], self.dde.ctypes.data
         d = B.PdPlanDesc(nx=self.nx, ny=self.ny, osf=2, nvis=self.nvis, uv=self.uv.ctypes.data,
                          nblocks=self.nblocks, block_of_vis=self.block_of_vis.ctypes.data,
                          kernel_width=int(kernel_width), kb_beta=float(kb_beta), nbases=self.nbases,
                          basis_ids=self.basis_ids.ctypes.data, levels=self.levels, precision=self.prec,
-                         tile=int(tile), g_mode=_G_MODE[g_mode])
+                         tile=int(tile), g_mode=_G_MODE[g_mode], dde_width=dde_w, dde_kernels=dde_ptr)
         h = ctypes.c_void_p()
         B.call("pd_plan_create", ctypes.byref(d), ctypes.byref(h))
         self._h = h

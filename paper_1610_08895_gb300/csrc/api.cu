@@ -136,8 +136,15 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         return fail(PD_EINVAL, "levels must satisfy 1 <= L <= 13 and n >> L >= 1");
     if (d->precision != PD_F32 && d->precision != PD_F64) return fail(PD_EINVAL, "precision must be PD_F32 or PD_F64");
     if (d->kb_beta < 0) return fail(PD_EINVAL, "kb_beta must be >= 0");
-    if (d->tile != 0 && (!is_pow2(d->tile) || d->tile < d->kernel_width))
-        return fail(PD_EINVAL, "tile must be 0 or a power of two >= kernel_width");
+    const int dde = d->dde_width > 1 ? d->dde_width : 0;
+    if (d->dde_width < 0 || (dde && ((dde & 1) == 0 || !d->dde_kernels)))
+        return fail(PD_EINVAL, "dde_width must be 0, 1 or odd >= 3 with dde_kernels given");
+    if (dde && d->g_mode != PD_G_CSR) return fail(PD_EINVAL, "DDE-aware G needs g_mode = PD_G_CSR");
+    if (dde && d->kernel_width + dde - 1 > 8)
+        return fail(PD_ENOTSUP, "DDE-aware G needs kernel_width + dde_width - 1 <= 8");
+    const int Jfoot = d->kernel_width + (dde ? dde - 1 : 0);   // footprint width of a row of G
+    if (d->tile != 0 && (!is_pow2(d->tile) || d->tile < Jfoot))
+        return fail(PD_EINVAL, "tile must be 0 or a power of two >= the kernel footprint");
     if (d->g_mode != PD_G_ON_THE_FLY && d->g_mode != PD_G_CSR)
         return fail(PD_EINVAL, "g_mode must be PD_G_ON_THE_FLY or PD_G_CSR");
     if (d->g_mode == PD_G_CSR && d->kernel_width > 8) return fail(PD_ENOTSUP, "the CSR form of G needs J <= 8");
@@ -148,8 +155,11 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
     p->csz = 2 * p->rsz;
     Geo& g = p->g;
     g.nx = d->nx; g.ny = d->ny; g.Kx = 2 * d->nx; g.Ky = 2 * d->ny;
-    g.J = d->kernel_width;
-    g.beta = d->kb_beta > 0 ? d->kb_beta : kb_beta_default(g.J);
+    p->kb_J = d->kernel_width;
+    p->dde = dde;
+    p->csr_cplx = dde > 0;
+    g.J = Jfoot;   // tiles, windows and halos follow the footprint; weights use kb_J
+    g.beta = d->kb_beta > 0 ? d->kb_beta : kb_beta_default(p->kb_J);
     // default tile: 32 cells (the densest tiles bound the gridding critical path); at least
     // two tiles per grid side, for the colour classes of the gridding
     int T = d->tile ? d->tile : 32;
@@ -322,6 +332,13 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
             fxs[i] = frx[m];
             fys[i] = fry[m];
         }
+        if (dde) {   // DDE kernels in internal order, for the CSR build below
+            const size_t per = (size_t)2 * dde * dde;
+            p->h_dde.resize((size_t)M * per);
+            for (int64_t i = 0; i < M; ++i)
+                std::copy(d->dde_kernels + (size_t)order[i] * per, d->dde_kernels + ((size_t)order[i] + 1) * per,
+                          p->h_dde.begin() + (size_t)i * per);
+        }
         ALLOC(p->cell, M);
         ALLOC(p->perm, M);
         CU(dalloc_bytes(A, B, &p->fx, M * p->rsz));
@@ -347,13 +364,13 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
         CU(dalloc_bytes(A, B, &p->cy, g.ny * p->rsz));
         CU(dalloc_bytes(A, B, &p->twx, g.Kx * p->csz));
         CU(dalloc_bytes(A, B, &p->twy, g.Ky * p->csz));
-        CU(upload_real(p->cx, deapodisation(g.nx, g.Kx, g.J, g.beta), p->prec));
-        CU(upload_real(p->cy, deapodisation(g.ny, g.Ky, g.J, g.beta), p->prec));
+        CU(upload_real(p->cx, deapodisation(g.nx, g.Kx, p->kb_J, g.beta), p->prec));
+        CU(upload_real(p->cy, deapodisation(g.ny, g.Ky, p->kb_J, g.beta), p->prec));
         CU(upload_real(p->twx, twiddles(g.Kx), p->prec));
         CU(upload_real(p->twy, twiddles(g.Ky), p->prec));
         {
-            std::vector<double> kp = kb_tap_polynomials(g.J, g.beta, KB_DEG);
-            for (int a = 0; a < g.J; ++a)
+            std::vector<double> kp = kb_tap_polynomials(p->kb_J, g.beta, KB_DEG);
+            for (int a = 0; a < p->kb_J; ++a)
                 for (int k = 0; k <= KB_DEG; ++k) p->kbpoly.c[a][k] = (float)kp[(size_t)a * (KB_DEG + 1) + k];
         }
         p->h_filt.assign((size_t)p->b * MAX_FILTER, 0.0);
@@ -396,11 +413,13 @@ static pd_status plan_build(pd_plan* p, const pd_plan_desc* d) {
     }
     if (p->g_mode == PD_G_CSR) {
         const size_t nnz = (size_t)g.J * g.J * (size_t)M;
-        if (dalloc(A, B, &p->csr_col, nnz) != cudaSuccess || dalloc_bytes(A, B, &p->csr_val, nnz * p->rsz) != cudaSuccess) {
+        if (dalloc(A, B, &p->csr_col, nnz) != cudaSuccess ||
+            dalloc_bytes(A, B, &p->csr_val, nnz * (p->csr_cplx ? p->csz : p->rsz)) != cudaSuccess) {
             (void)cudaGetLastError();
             return fail(PD_ENOMEM, "the CSR form of G does not fit in device memory");
         }
         CU(build_csr(p, 0));
+        std::vector<double>().swap(p->h_dde);
     }
 #undef ALLOC
     CU(cudaDeviceSynchronize());

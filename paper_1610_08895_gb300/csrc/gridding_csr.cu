@@ -17,6 +17,7 @@
 //   the warp's private copy of the window (the J^2 cells of one footprint are distinct,
 //   so no atomics), the warps' copies are summed in warp order into U. Deterministic.
 #include <algorithm>
+#include <type_traits>
 
 #include "gridding.cuh"
 
@@ -50,12 +51,76 @@ __global__ void k_build_csr(const int32_t* __restrict__ cell, const R* __restric
     }
 }
 
+// Row m of the DDE-aware G (Sec. 2): the JK x JK interpolation kernel convolved with the
+// point's d x d Fourier-domain DDE kernel D_m (offsets -h .. h), a footprint of
+// g.J = JK + d - 1 cells per axis starting g.halo_lo = JK/2 - 1 + h cells before the base
+// cell. Entry (b', a') = sum over b + i = b', a + j = a' of phi_y(b) phi_x(a) D_m[i][j],
+// summed in FP64 and rounded once.
+template <typename R, int JK>
+__global__ void k_build_csr_dde(const int32_t* __restrict__ cell, const R* __restrict__ fxs,
+                                const R* __restrict__ fys, const double2* __restrict__ dde, int dw, int64_t M,
+                                Geo g, double beta, int32_t* __restrict__ col, cplx_t<R>* __restrict__ val) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double wx[JK], wy[JK];
+    const double toj = 2.0 / JK;
+#pragma unroll
+    for (int a = 0; a < JK; ++a) {
+        wx[a] = kb_weight<double>((double)fxs[m] + (JK / 2 - 1 - a), toj, beta);
+        wy[a] = kb_weight<double>((double)fys[m] + (JK / 2 - 1 - a), toj, beta);
+    }
+    const int c = cell[m], by = c >> 16, bx = c & 0xFFFF;
+    const int Jf = g.J;
+    const double2* D = dde + m * dw * dw;
+    int32_t* cp = col + m * Jf * Jf;
+    cplx_t<R>* vp = val + m * Jf * Jf;
+    for (int bq = 0; bq < Jf; ++bq) {
+        const int ky = (by - g.halo_lo + bq) & (g.Ky - 1);
+        for (int aq = 0; aq < Jf; ++aq) {
+            double re = 0.0, im = 0.0;
+            for (int i = 0; i < dw; ++i) {
+                const int b = bq - i;
+                if (b < 0 || b >= JK) continue;
+                for (int j = 0; j < dw; ++j) {
+                    const int a = aq - j;
+                    if (a < 0 || a >= JK) continue;
+                    const double w = wy[b] * wx[a];
+                    re += w * D[i * dw + j].x;
+                    im += w * D[i * dw + j].y;
+                }
+            }
+            cp[bq * Jf + aq] = (ky << 16) | ((bx - g.halo_lo + aq) & (g.Kx - 1));
+            vp[bq * Jf + aq] = mk<cplx_t<R>>((R)re, (R)im);
+        }
+    }
+}
+
 cudaError_t build_csr(pd_plan* p, cudaStream_t s) {
     const Geo& g = p->g;
     const int64_t M = p->M;
     const unsigned nb = (unsigned)((M + 127) / 128);
     if (M == 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
+    if (p->csr_cplx) {
+        // the DDE kernels go to the device once, for this build only
+        double2* dd = nullptr;
+        const size_t bytes = p->h_dde.size() * sizeof(double);
+        if ((e = cudaMalloc(&dd, bytes))) return e;
+        if ((e = cudaMemcpy(dd, p->h_dde.data(), bytes, cudaMemcpyHostToDevice))) { cudaFree(dd); return e; }
+        if (p->prec == PD_F64) {
+            PD_J_DISPATCH(p->kb_J, (k_build_csr_dde<double, JJ><<<nb, 128, 0, s>>>(
+                                       p->cell, (const double*)p->fx, (const double*)p->fy, dd, p->dde, M, g,
+                                       g.beta, p->csr_col, (double2*)p->csr_val)));
+        } else {
+            PD_J_DISPATCH(p->kb_J, (k_build_csr_dde<float, JJ><<<nb, 128, 0, s>>>(
+                                       p->cell, (const float*)p->fx, (const float*)p->fy, dd, p->dde, M, g,
+                                       g.beta, p->csr_col, (float2*)p->csr_val)));
+        }
+        if (!e) e = cudaGetLastError();
+        const cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(dd);
+        return e ? e : e2;
+    }
     if (p->prec == PD_F64) {
         PD_J_DISPATCH(g.J, (k_build_csr<double, JJ><<<nb, 128, 0, s>>>(p->cell, (const double*)p->fx,
                                                                        (const double*)p->fy, M, g, p->csr_col,
@@ -68,14 +133,46 @@ cudaError_t build_csr(pd_plan* p, cudaStream_t s) {
     return e ? e : cudaGetLastError();
 }
 
+// Weight arithmetic for real rows (interpolation only) and complex rows (DDE-aware G):
+// wmac: s += w g; wmacc: a += conj(w) v (the adjoint's weight).
+__device__ __forceinline__ void wmac(float w, float2 g, float& sx, float& sy) { sx += w * g.x; sy += w * g.y; }
+__device__ __forceinline__ void wmac(double w, double2 g, double& sx, double& sy) { sx += w * g.x; sy += w * g.y; }
+__device__ __forceinline__ void wmac(float2 w, float2 g, float& sx, float& sy) {
+    sx += w.x * g.x - w.y * g.y;
+    sy += w.x * g.y + w.y * g.x;
+}
+__device__ __forceinline__ void wmac(double2 w, double2 g, double& sx, double& sy) {
+    sx += w.x * g.x - w.y * g.y;
+    sy += w.x * g.y + w.y * g.x;
+}
+__device__ __forceinline__ void wmacc(float w, float vr, float vi, float2& a) { a.x += w * vr; a.y += w * vi; }
+__device__ __forceinline__ void wmacc(double w, double vr, double vi, double2& a) { a.x += w * vr; a.y += w * vi; }
+__device__ __forceinline__ void wmacc(float2 w, float vr, float vi, float2& a) {
+    a.x += w.x * vr + w.y * vi;
+    a.y += w.x * vi - w.y * vr;
+}
+__device__ __forceinline__ void wmacc(double2 w, double vr, double vi, double2& a) {
+    a.x += w.x * vr + w.y * vi;
+    a.y += w.x * vi - w.y * vr;
+}
+
 // J consecutive entries of one footprint row (16-byte loads where the row is 16-byte aligned)
-template <typename R, int J>
-__device__ __forceinline__ void load_row(const int32_t* __restrict__ cp, const R* __restrict__ vp, int* cc, R* ww) {
-    if constexpr (J == 8 && sizeof(R) == 4) {
+template <typename W, int J>
+__device__ __forceinline__ void load_row(const int32_t* __restrict__ cp, const W* __restrict__ vp, int* cc, W* ww) {
+    if constexpr (J == 8 && std::is_same<W, float>::value) {
         const int4 c0 = *reinterpret_cast<const int4*>(cp), c1 = *reinterpret_cast<const int4*>(cp + 4);
         const float4 v0 = *reinterpret_cast<const float4*>(vp), v1 = *reinterpret_cast<const float4*>(vp + 4);
         cc[0] = c0.x; cc[1] = c0.y; cc[2] = c0.z; cc[3] = c0.w; cc[4] = c1.x; cc[5] = c1.y; cc[6] = c1.z; cc[7] = c1.w;
         ww[0] = v0.x; ww[1] = v0.y; ww[2] = v0.z; ww[3] = v0.w; ww[4] = v1.x; ww[5] = v1.y; ww[6] = v1.z; ww[7] = v1.w;
+    } else if constexpr (J == 8 && std::is_same<W, float2>::value) {
+        const int4 c0 = *reinterpret_cast<const int4*>(cp), c1 = *reinterpret_cast<const int4*>(cp + 4);
+        cc[0] = c0.x; cc[1] = c0.y; cc[2] = c0.z; cc[3] = c0.w; cc[4] = c1.x; cc[5] = c1.y; cc[6] = c1.z; cc[7] = c1.w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = *reinterpret_cast<const float4*>(vp + 2 * q);
+            ww[2 * q] = make_float2(v.x, v.y);
+            ww[2 * q + 1] = make_float2(v.z, v.w);
+        }
     } else {
 #pragma unroll
         for (int a = 0; a < J; ++a) { cc[a] = cp[a]; ww[a] = vp[a]; }
@@ -86,11 +183,11 @@ __device__ __forceinline__ void load_row(const int32_t* __restrict__ cp, const R
 // MODE 0: out_user[perm[m]] = (G grid)_m; MODE 1: r = v + G b - y for visibilities of
 // active blocks with the FP64 per-segment sums of ||r||^2 and ||G b - y||^2 (the outputs
 // of the on-the-fly degridding, same work items and tile claiming).
-template <typename R, int J, int MODE>
+template <typename R, typename W, int J, int MODE>
 __global__ void __launch_bounds__(256) k_degrid_csr(
     const cplx_t<R>* __restrict__ grid, cplx_t<R>* __restrict__ out, const cplx_t<R>* __restrict__ y,
     const cplx_t<R>* __restrict__ v, cplx_t<R>* __restrict__ rbuf, const int32_t* __restrict__ col,
-    const R* __restrict__ val, const int32_t* __restrict__ perm, const int32_t* __restrict__ seg_start,
+    const W* __restrict__ val, const int32_t* __restrict__ perm, const int32_t* __restrict__ seg_start,
     const int32_t* __restrict__ seg_block, const int32_t* __restrict__ tile_seg_start,
     const int32_t* __restrict__ active, const int32_t* __restrict__ list, const int32_t* __restrict__ count,
     double* __restrict__ seg_part, int max_segs, Geo g, int* __restrict__ next_tile, int batch, int64_t gstride,
@@ -140,14 +237,12 @@ __global__ void __launch_bounds__(256) k_degrid_csr(
                 m = seg_start[act_seg[j]] + pos - act_pre[j];
                 if (b < J) {
                     int cc[J];
-                    R ww[J];
-                    load_row<R, J>(col + (int64_t)m * (J * J) + b * J, val + (int64_t)m * (J * J) + b * J, cc, ww);
+                    W ww[J];
+                    load_row<W, J>(col + (int64_t)m * (J * J) + b * J, val + (int64_t)m * (J * J) + b * J, cc, ww);
 #pragma unroll
                     for (int a = 0; a < J; ++a) {
                         const int ey = ((cc[a] >> 16) - wy0) & (g.Ky - 1), ex = ((cc[a] & 0xFFFF) - wx0) & (g.Kx - 1);
-                        const C2 gv = win[ey * E + ex];
-                        sx += ww[a] * gv.x;
-                        sy += ww[a] * gv.y;
+                        wmac(ww[a], win[ey * E + ex], sx, sy);
                     }
                 }
             }
@@ -188,26 +283,33 @@ __global__ void __launch_bounds__(256) k_degrid_csr(
     }
 }
 
-template <typename R, int J, int MODE>
-cudaError_t launch_degrid_csr(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out, const DualArgs* a,
-                              const int32_t* tiles, const int32_t* count, int ctas, cudaStream_t s, int batch) {
+template <typename R, typename W, int J, int MODE>
+static cudaError_t degrid_csr_w(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out, const DualArgs* a,
+                                const int32_t* tiles, const int32_t* count, int ctas, cudaStream_t s, int batch) {
     const Geo& g = p->g;
     const int ms = std::max(p->max_tile_segs, 1);
     const size_t win = (size_t)g.ext * g.ext + (g.ext * g.ext & 1);
     const size_t smem = win * sizeof(cplx_t<R>) + (size_t)16 * ms * sizeof(double) + (size_t)(2 * ms + 1) * sizeof(int);
-    cudaError_t e = ensure_smem(k_degrid_csr<R, J, MODE>, smem);
+    cudaError_t e = ensure_smem(k_degrid_csr<R, W, J, MODE>, smem);
     if (e) return e;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid_csr<R, J, MODE>, 256, smem) == cudaSuccess &&
-        per_sm > 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid_csr<R, W, J, MODE>, 256, smem) ==
+            cudaSuccess && per_sm > 0)
         ctas = std::min(ctas, per_sm * p->num_sms);
     if ((e = cudaMemsetAsync(p->sched + 4, 0, sizeof(int32_t), s))) return e;
-    k_degrid_csr<R, J, MODE><<<ctas, 256, smem, s>>>(
+    k_degrid_csr<R, W, J, MODE><<<ctas, 256, smem, s>>>(
         grid, out, a ? (const cplx_t<R>*)a->y : nullptr, a ? (const cplx_t<R>*)a->v : nullptr,
-        (cplx_t<R>*)p->rbuf, p->csr_col, (const R*)p->csr_val, p->perm, p->seg_start, p->seg_block,
+        (cplx_t<R>*)p->rbuf, p->csr_col, (const W*)p->csr_val, p->perm, p->seg_start, p->seg_block,
         p->tile_seg_start, a ? a->block_active : nullptr, tiles, count, p->seg_part, ms, g, p->sched + 4, batch,
         (int64_t)(g.nx / 4 + 1) * 4 * g.Ky, (int64_t)p->M);
     return cudaGetLastError();
+}
+
+template <typename R, int J, int MODE>
+cudaError_t launch_degrid_csr(const pd_plan* p, const cplx_t<R>* grid, cplx_t<R>* out, const DualArgs* a,
+                              const int32_t* tiles, const int32_t* count, int ctas, cudaStream_t s, int batch) {
+    return p->csr_cplx ? degrid_csr_w<R, cplx_t<R>, J, MODE>(p, grid, out, a, tiles, count, ctas, s, batch)
+                       : degrid_csr_w<R, R, J, MODE>(p, grid, out, a, tiles, count, ctas, s, batch);
 }
 
 // ---------------------------------------------------------------- gridding
@@ -220,6 +322,12 @@ template <typename R> __device__ __forceinline__ void ld2(const R* p, R& a, R& b
         a = q.x; b = q.y;
     }
 }
+
+__device__ __forceinline__ void ld2(const float2* p, float2& a, float2& b) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    a = make_float2(q.x, q.y); b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void ld2(const double2* p, double2& a, double2& b) { a = p[0]; b = p[1]; }
 
 // The raw inputs of one visibility to grid: MODE 1 r, v_old and the block's ball scale;
 // MODE 0 the input value (in a).
@@ -260,11 +368,11 @@ __device__ __forceinline__ cplx_t<R> grid_raw_value(const GridRaw<R>& in, cplx_t
 // Each warp takes a contiguous share of the tile's active visibilities (fixed by the
 // warp index, so the summation order is too) and adds them one at a time into its own
 // E x E window; the windows are then summed in warp order and added to U.
-template <typename R, int J, int MODE>
+template <typename R, typename W, int J, int MODE>
 __global__ void __launch_bounds__(256, 2) k_grid_csr(
     const cplx_t<R>* __restrict__ src, const cplx_t<R>* __restrict__ rbuf, cplx_t<R>* __restrict__ v,
     const R* __restrict__ scale, const int32_t* __restrict__ active, const int32_t* __restrict__ col,
-    const R* __restrict__ val, const int32_t* __restrict__ perm, const int32_t* __restrict__ seg_start,
+    const W* __restrict__ val, const int32_t* __restrict__ perm, const int32_t* __restrict__ seg_start,
     const int32_t* __restrict__ seg_block, const int32_t* __restrict__ tile_seg_start,
     const int32_t* __restrict__ list, const int32_t* __restrict__ count, cplx_t<R>* __restrict__ U, int max_segs,
     Geo g, int* __restrict__ next_tile, int batch, int64_t sstride, int64_t ustride) {
@@ -314,16 +422,16 @@ __global__ void __launch_bounds__(256, 2) k_grid_csr(
                 grid_raw<R, MODE>(nx, q0 + 32 + lane, j, act_seg, act_pre, seg_start, seg_block, simg, rbuf, v, perm, scale);
             for (int qb = 0; qb < nq; qb += PB) {
                 int2 cc[PB];
-                R w0[PB], w1[PB];
+                W w0[PB], w1[PB];
 #pragma unroll
                 for (int k = 0; k < PB; ++k) {
                     const int mq = __shfl_sync(0xffffffffu, cur.m, (qb + k) & 31);
                     cc[k] = make_int2(0, 0);
-                    w0[k] = w1[k] = R(0);
+                    w0[k] = w1[k] = W{};
                     if (has && qb + k < nq) {
                         const int64_t o = (int64_t)mq * NE + e0;
                         cc[k] = *reinterpret_cast<const int2*>(col + o);
-                        ld2(val + o, w0[k], w1[k]);
+                        ld2(val + o, w0[k], w1[k]);   // entries e0, e0 + 1 (16-byte aligned pair)
                     }
                 }
 #pragma unroll
@@ -334,12 +442,10 @@ __global__ void __launch_bounds__(256, 2) k_grid_csr(
                         const int i0 = (((cc[k].x >> 16) - wy0) & (g.Ky - 1)) * E + (((cc[k].x & 0xFFFF) - wx0) & (g.Kx - 1));
                         const int i1 = (((cc[k].y >> 16) - wy0) & (g.Ky - 1)) * E + (((cc[k].y & 0xFFFF) - wx0) & (g.Kx - 1));
                         C2 a0 = win[i0];
-                        a0.x += w0[k] * vr;
-                        a0.y += w0[k] * vi;
+                        wmacc(w0[k], vr, vi, a0);
                         win[i0] = a0;
                         C2 a1 = win[i1];
-                        a1.x += w1[k] * vr;
-                        a1.y += w1[k] * vi;
+                        wmacc(w1[k], vr, vi, a1);
                         win[i1] = a1;
                     }
                     __syncwarp();     // the next visibility's lanes may read these cells
@@ -356,26 +462,33 @@ __global__ void __launch_bounds__(256, 2) k_grid_csr(
     }
 }
 
-template <typename R, int J, int MODE>
-cudaError_t launch_grid_csr(const pd_plan* p, const cplx_t<R>* src, const DualArgs* a, const int32_t* tiles,
-                            const int32_t* count, cplx_t<R>* U, int* next_tile, cudaStream_t s, int batch) {
+template <typename R, typename W, int J, int MODE>
+static cudaError_t grid_csr_w(const pd_plan* p, const cplx_t<R>* src, const DualArgs* a, const int32_t* tiles,
+                              const int32_t* count, cplx_t<R>* U, int* next_tile, cudaStream_t s, int batch) {
     const Geo& g = p->g;
     const int ms = std::max(p->max_tile_segs, 1);
     const size_t winb = (size_t)g.ext * g.ext * sizeof(cplx_t<R>);
     // eight warps unless their windows do not fit (large tiles in FP64)
     const int nw = (int)std::max<size_t>(1, std::min<size_t>(8, ((size_t)200 << 10) / winb));
     const size_t smem = nw * winb + (size_t)(2 * ms + 1) * sizeof(int);
-    cudaError_t e = ensure_smem(k_grid_csr<R, J, MODE>, smem);
+    cudaError_t e = ensure_smem(k_grid_csr<R, W, J, MODE>, smem);
     if (e) return e;
     int per_sm = 0, ctas = std::min(g.ntiles * batch, p->num_sms * 8);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_csr<R, J, MODE>, nw * 32, smem) ==
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_csr<R, W, J, MODE>, nw * 32, smem) ==
             cudaSuccess && per_sm > 0)
         ctas = std::min(ctas, per_sm * p->num_sms);
-    k_grid_csr<R, J, MODE><<<ctas, nw * 32, smem, s>>>(
+    k_grid_csr<R, W, J, MODE><<<ctas, nw * 32, smem, s>>>(
         src, (const cplx_t<R>*)p->rbuf, a ? (cplx_t<R>*)a->v : nullptr, (const R*)p->blk_scale,
-        a ? a->block_active : nullptr, p->csr_col, (const R*)p->csr_val, p->perm, p->seg_start, p->seg_block,
+        a ? a->block_active : nullptr, p->csr_col, (const W*)p->csr_val, p->perm, p->seg_start, p->seg_block,
         p->tile_seg_start, tiles, count, U, ms, g, next_tile, batch, (int64_t)p->M, (int64_t)g.Kx * g.Ky);
     return cudaGetLastError();
+}
+
+template <typename R, int J, int MODE>
+cudaError_t launch_grid_csr(const pd_plan* p, const cplx_t<R>* src, const DualArgs* a, const int32_t* tiles,
+                            const int32_t* count, cplx_t<R>* U, int* next_tile, cudaStream_t s, int batch) {
+    return p->csr_cplx ? grid_csr_w<R, cplx_t<R>, J, MODE>(p, src, a, tiles, count, U, next_tile, s, batch)
+                       : grid_csr_w<R, R, J, MODE>(p, src, a, tiles, count, U, next_tile, s, batch);
 }
 
 #define PD_CSR_INST(R_, J_)                                                                                      \

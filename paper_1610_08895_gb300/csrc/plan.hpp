@@ -74,6 +74,10 @@ struct pd_plan {
     void* fy = nullptr;
     int32_t* perm = nullptr;       // internal -> user index
     int g_mode = PD_G_ON_THE_FLY;  // PD_G_CSR: G stored explicitly, below
+    int kb_J = 0;                  // interpolation kernel width (g.J is the footprint: kb_J + dde - 1)
+    int dde = 0;                   // DDE kernel width d (0: none)
+    bool csr_cplx = false;         // CSR entries complex (DDE-aware G)
+    std::vector<double> h_dde;     // DDE kernels, internal order (kept until G is built)
     int32_t* csr_col = nullptr;    // [J^2][M] grid cell (ky << 16 | kx) of each entry, internal order
     void* csr_val = nullptr;       // real [J^2][M] weight of each entry
     int32_t* seg_start = nullptr;  // [nseg + 1]

@@ -61,6 +61,7 @@ def test_plan_descriptions_are_refused_before_any_device_work(lib):
     blk = np.zeros(m, np.int32)
     ids = np.array([0, 1], np.int32)
     bad_ids = np.array([0, 9], np.int32)
+    dde = np.zeros((m, 3, 3, 2))
 
     def create(**over):
         kw = dict(nx=64, ny=64, osf=2, nvis=m, uv=uv.ctypes.data, nblocks=1, block_of_vis=blk.ctypes.data,
@@ -85,6 +86,10 @@ def test_plan_descriptions_are_refused_before_any_device_work(lib):
         (dict(precision=7), 1, b"precision"),
         (dict(g_mode=2), 1, b"g_mode"),
         (dict(g_mode=B.PD_G_CSR, kernel_width=10), 6, b"CSR"),
+        (dict(dde_width=3, dde_kernels=dde.ctypes.data), 1, b"PD_G_CSR"),
+        (dict(g_mode=B.PD_G_CSR, dde_width=2, dde_kernels=dde.ctypes.data), 1, b"odd"),
+        (dict(g_mode=B.PD_G_CSR, dde_width=3), 1, b"dde_kernels"),
+        (dict(g_mode=B.PD_G_CSR, dde_width=3, dde_kernels=dde.ctypes.data), 6, b"<= 8"),
     ]
     for over, status, text in cases:
         st, msg = create(**over)
