@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-sara", action="store_true")
     ap.add_argument("--no-dde", action="store_true")
+    ap.add_argument("--no-synthesis", action="store_true")
     ap.add_argument("--csr-steps", type=int, default=20)
     ap.add_argument("--g-mode", default="on_the_fly", choices=["on_the_fly", "csr"],
                     help="form of G for --profile-run")
@@ -461,6 +462,11 @@ def run_ours(args):
     if not args.no_dde:
         dde = run_dde(args, cfg, uv, blk, d, tile, y, eps, kw, stream)
 
+    # ---- the synthesis formulation on the same data (eager iterations)
+    synthesis = None
+    if not args.no_synthesis:
+        synthesis = run_synthesis(plan, y, eps, kw, stream)
+
     # ---- errors of this run's results against the FP64 oracle on sampled outputs
     errors = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -484,7 +490,7 @@ def run_ours(args):
                        "graph": "one CUDA graph per iteration, replayed", "setup_s": round(setup_s, 1),
                        "plan": info},
             "roofline": roofline, "kernels": kernels, "clocks": clk.summary(), "e2e": e2e,
-            "fp64": fp64, "csr": csr, "sara": sara, "dde": dde, "operators": operators, "cpu_baseline": cpu, "errors": errors,
+            "fp64": fp64, "csr": csr, "sara": sara, "dde": dde, "synthesis": synthesis, "operators": operators, "cpu_baseline": cpu, "errors": errors,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -601,6 +607,29 @@ def run_dde(args, cfg, uv, blk, d, tile, y, eps, kw, stream, steps=10):
             "steps": steps, "kernels_ms": kern, "plan_s": round(setup, 1), "device_bytes": info.get("device_bytes"),
             "form": "FP32 batched graph; G = 6x6 Kaiser-Bessel kernel convolved with a 3x3 complex DDE kernel per "
                     "visibility, complex CSR rows of 64 entries"}
+
+
+def run_synthesis(plan, y, eps, kw, stream, steps=10):
+    """Eager iterations of the synthesis formulation (pd_synthesis_iterate): x = Psi alpha,
+    l1 on the coefficients, positivity as a dual; same data, blocks and draws."""
+    import torch
+    from paper_1610_08895_gb300.api import State
+    st = State(plan)
+    st.pd_state_set_data(y, eps)
+    args = dict(tau=kw["tau"], sigma=1.0, varsigma=kw["varsigma"], kappa=kw["kappa"], seed=kw["seed"],
+                p_block=kw["p_block"])
+    st.pd_synthesis_iterate(2, **args)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st.pd_synthesis_iterate(steps, **args)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st.close()
+    return {"value": round(steps / (ms / 1e3), 3), "unit": "PD iters/s", "ms_per_step": round(ms / steps, 4),
+            "steps": steps, "form": "FP32, eager (one call of `steps` iterations, the image Psi alpha formed "
+                                    "once at the end); every coefficient updated every iteration"}
 
 
 # ---------------------------------------------------------------------------------------------

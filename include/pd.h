@@ -313,6 +313,26 @@ pd_status pd_iterate(pd_plan* plan, pd_state* st, const pd_params* params, int32
                      void* stream);
 
 /*
+ * The synthesis formulation (Sec. 2 names a synthesis approach beside the analysis
+ * problem): x = Psi alpha with alpha the [nbases][ny][nx] coefficients of the same
+ * normalised dictionary, minimise kappa ||alpha||_1 subject to ||y_i - Phi_i Psi alpha||
+ * <= eps_i for every block and Psi alpha >= 0, by niter iterations of the primal-dual
+ * template of Algorithm 1 with the roles of the two non-smooth terms exchanged:
+ * draw the active blocks (params->p_block, seed; the same Philox draws), x~ = Psi alpha~,
+ * the ball dual update of steps 5-8 for the active blocks, the positivity dual
+ * u <- min(u + x~, 0), then alpha <- S_{tau kappa}(alpha - tau Psi^H(sigma u + varsigma
+ * Re(Phi^H v))) and alpha~ = 2 alpha_new - alpha. Uses tau, sigma, varsigma, kappa,
+ * seed and p_block of params (p_basis is ignored: every coefficient is updated);
+ * adaptive, per_block, use_graph and profile must be 0. The state's s holds alpha
+ * (pd_state_get_s) and, after the call, x holds Psi alpha (pd_state_get_x); start from
+ * pd_state_set_data (zeros). A state iterated in this form must not be passed to
+ * pd_iterate before pd_state_set_data resets it. Synchronises `stream` before
+ * returning. Errors: PD_EINVAL, PD_ENOMEM, PD_ECUDA.
+ */
+pd_status pd_synthesis_iterate(pd_plan* plan, pd_state* st, const pd_params* params, int32_t niter,
+                               void* stream);
+
+/*
  * One iteration split at its only exchange point, for a problem whose data blocks are
  * spread over several GPUs (Sec. 3: the data blocks are processed in parallel and only
  * sum_i G_i^T v_i travels back to the primal update). Each rank plans its own

@@ -69,6 +69,7 @@ _SIGS = {
     "pd_state_set_data": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "pd_state_set_start": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "pd_iterate": ([_VP, _VP, ctypes.POINTER(PdParams), ctypes.c_int32, _VP], ctypes.c_int),
+    "pd_synthesis_iterate": ([_VP, _VP, ctypes.POINTER(PdParams), ctypes.c_int32, _VP], ctypes.c_int),
     "pd_iterate_dual": ([_VP, _VP, ctypes.POINTER(PdParams), _VP], ctypes.c_int),
     "pd_iterate_primal": ([_VP, _VP, ctypes.POINTER(PdParams), _VP, _VP], ctypes.c_int),
     "pd_state_u": ([_VP, ctypes.POINTER(_VP), _VP], ctypes.c_int),

@@ -231,6 +231,15 @@ class State:
             prm.adapt_exact = int(bool(adaptive.get("exact", False)))
         B.call("pd_iterate", p.handle, self._h, ctypes.byref(prm), int(niter), _stream())
 
+    def pd_synthesis_iterate(self, niter, tau, sigma, varsigma, kappa, seed=0, p_block=None):
+        """pd_synthesis_iterate: the synthesis formulation (x = Psi alpha, l1 on alpha,
+        positivity as a dual); alpha is read with s(), the image with x()."""
+        p = self.plan
+        pb = np.ascontiguousarray(np.ones(p.nblocks) if p_block is None else p_block, dtype=np.float64)
+        prm = B.PdParams(tau=tau, sigma=sigma, varsigma=varsigma, kappa=kappa, psi_norm=1.0, seed=int(seed),
+                         p_block=pb.ctypes.data, p_basis=None)
+        B.call("pd_synthesis_iterate", p.handle, self._h, ctypes.byref(prm), int(niter), _stream())
+
     def x(self):
         p = self.plan
         out = torch.empty((p.ny, p.nx), dtype=p.real_dtype, device="cuda")

@@ -670,6 +670,8 @@ extern "C" pd_status pd_state_set_data(pd_plan* p, pd_state* st, const void* y, 
     CU(cudaMemsetAsync(st->u, 0, K * p->csz, s));
     CU(cudaMemsetAsync(st->t, 0, sizeof(int64_t), s));
     CU(cudaMemsetAsync(st->diag, 0, 2 * sizeof(double), s));
+    if (st->syn_at) CU(cudaMemsetAsync(st->syn_at, 0, N * p->b * p->rsz, s));
+    if (st->syn_u) CU(cudaMemsetAsync(st->syn_u, 0, N * p->rsz, s));
     std::vector<double> ones_d(p->d, 1.0), ones_b(p->b, 1.0);
     CU(cudaMemcpyAsync(st->p_block, ones_d.data(), p->d * sizeof(double), cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(st->p_basis, ones_b.data(), p->b * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -934,6 +936,65 @@ extern "C" pd_status pd_state_u(pd_state* st, void** u, int64_t* elements) {
     if (!st || !u) return fail(PD_EINVAL, "pd_state_u: bad argument");
     *u = st->u;
     if (elements) *elements = (int64_t)st->plan->g.Kx * st->plan->g.Ky;
+    return PD_OK;
+}
+
+// Synthesis form (x = Psi alpha, l1 on the coefficients, positivity as a dual): one
+// iteration of the primal-dual template of Algorithm 1 with the roles of the two
+// non-smooth terms exchanged. alpha lives in the state's s, x~ in xt; st is scratch.
+template <typename R>
+static cudaError_t enqueue_synthesis(pd_plan* p, pd_state* st, const pd_params* prm, cudaStream_t s) {
+    cudaError_t e;
+    SelectArgs sa{prm->seed, 0, 0.0, 0.0, 0.0};
+    if ((e = select_active(p, st, sa, s))) return e;                                      // step 3
+    if ((e = psi_plain<R>(p, (const R*)st->syn_at, (R*)st->xt, s))) return e;            // x~ = Psi alpha~
+    if ((e = fwd_fft<R>(p, (const R*)st->xt, (cplx_t<R>*)p->gridb, s))) return e;        // b~ = F Z x~
+    DualArgs da{st->y, st->v, st->block_active, st->eps, st->res_norm};
+    if ((e = degrid_dual<R>(p, (const cplx_t<R>*)p->gridb, da, st->act_tiles, st->counts, s))) return e;
+    {
+        const int q = p->g.ntiles / 4;
+        const int32_t* lists[4] = {st->act_col, st->act_col + q, st->act_col + 2 * q, st->act_col + 3 * q};
+        if ((e = grid_dual<R>(p, da, lists, st->counts + 2, (cplx_t<R>*)st->u, s))) return e;
+    }
+    if ((e = inv_fft<R>(p, (const cplx_t<R>*)st->u, (R*)st->st, nullptr, s))) return e;  // Re(Phi^H v)
+    if ((e = synth_dual<R>(p, (const R*)st->xt, (R*)st->syn_u, (R*)st->st, prm->sigma, prm->varsigma, s)))
+        return e;
+    if ((e = psi_adj_plain<R>(p, (const R*)st->st, (R*)p->ds, s))) return e;
+    return synth_primal<R>(p, (R*)st->s, (R*)st->syn_at, (const R*)p->ds, prm->tau, prm->tau * prm->kappa, s);
+}
+
+extern "C" pd_status pd_synthesis_iterate(pd_plan* p, pd_state* st, const pd_params* prm, int32_t niter,
+                                          void* stream) {
+    if (!p || !st || !prm || st->plan != p || niter < 0) return fail(PD_EINVAL, "pd_synthesis_iterate: bad argument");
+    if (!prm->p_block) return fail(PD_EINVAL, "pd_synthesis_iterate: missing block probabilities");
+    if (prm->adaptive || prm->per_block || prm->use_graph || prm->profile)
+        return fail(PD_EINVAL, "pd_synthesis_iterate: adaptive, per_block, use_graph and profile must be 0");
+    for (int i = 0; i < p->d; ++i)
+        if (!(prm->p_block[i] > 0 && prm->p_block[i] <= 1)) return fail(PD_EINVAL, "p_block must lie in (0, 1]");
+    if (!(prm->tau > 0)) return fail(PD_EINVAL, "pd_synthesis_iterate: tau must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)p->g.nx * p->g.ny;
+    if (!st->syn_at) {
+        size_t& B = st->device_bytes;
+        if (dalloc_bytes(st->allocs, B, &st->syn_at, N * p->b * p->rsz) ||
+            dalloc_bytes(st->allocs, B, &st->syn_u, N * p->rsz)) {
+            (void)cudaGetLastError();
+            return fail(PD_ENOMEM, "pd_synthesis_iterate: device allocation failed");
+        }
+        CU(cudaMemsetAsync(st->syn_at, 0, N * p->b * p->rsz, s));
+        CU(cudaMemsetAsync(st->syn_u, 0, N * p->rsz, s));
+    }
+    std::vector<double> ones(p->b, 1.0);   // every basis: the coefficients are primal
+    CU(cudaMemcpyAsync(st->p_block, prm->p_block, p->d * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(st->p_basis, ones.data(), p->b * sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < niter; ++k) {
+        if (p->prec == PD_F64) CU(enqueue_synthesis<double>(p, st, prm, s));
+        else CU(enqueue_synthesis<float>(p, st, prm, s));
+    }
+    // the image x = Psi alpha for pd_state_get_x
+    if (p->prec == PD_F64) CU(psi_plain<double>(p, (const double*)st->s, (double*)st->x, s));
+    else CU(psi_plain<float>(p, (const float*)st->s, (float*)st->x, s));
+    CU(cudaStreamSynchronize(s));   // the host vector of ones is read by the copy above
     return PD_OK;
 }
 

@@ -300,6 +300,54 @@ cudaError_t init_res_norm(const pd_plan* p, pd_state* st, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Synthesis form, dual of positivity and the image-domain term of the primal step:
+// u <- min(u + x~, 0) (z - P_C(z)); back <- sigma u + varsigma back.
+template <typename R>
+__global__ void k_synth_dual(const R* __restrict__ xt, R* __restrict__ u, R* __restrict__ back, int64_t n, R sigma,
+                             R varsigma) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R z = u[i] + xt[i];
+        const R un = z < R(0) ? z : R(0);
+        u[i] = un;
+        back[i] = sigma * un + varsigma * back[i];
+    }
+}
+
+// Synthesis form, primal step on the coefficients: alpha_new = S_thr(alpha - tau w)
+// (eq. prox-L1), alpha~ = 2 alpha_new - alpha, alpha = alpha_new.
+template <typename R>
+__global__ void k_synth_primal(R* __restrict__ alpha, R* __restrict__ alpha_t, const R* __restrict__ w, int64_t n,
+                               R tau, R thr) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R a = alpha[i];
+        const R q = a - tau * w[i];
+        const R an = q > thr ? q - thr : (q < -thr ? q + thr : R(0));
+        alpha_t[i] = R(2) * an - a;
+        alpha[i] = an;
+    }
+}
+
+template <typename R>
+cudaError_t synth_dual(const pd_plan* p, const R* xt, R* u, R* back, double sigma, double varsigma, cudaStream_t s) {
+    const int64_t n = (int64_t)p->g.nx * p->g.ny;
+    const int ctas = (int)std::min<int64_t>((n + 255) / 256, (int64_t)p->num_sms * 8);
+    k_synth_dual<R><<<ctas, 256, 0, s>>>(xt, u, back, n, (R)sigma, (R)varsigma);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t synth_primal(const pd_plan* p, R* alpha, R* alpha_t, const R* w, double tau, double thr, cudaStream_t s) {
+    const int64_t n = (int64_t)p->b * p->g.nx * p->g.ny;
+    const int ctas = (int)std::min<int64_t>((n + 255) / 256, (int64_t)p->num_sms * 8);
+    k_synth_primal<R><<<ctas, 256, 0, s>>>(alpha, alpha_t, w, n, (R)tau, (R)thr);
+    return cudaGetLastError();
+}
+
+template cudaError_t synth_dual<float>(const pd_plan*, const float*, float*, float*, double, double, cudaStream_t);
+template cudaError_t synth_dual<double>(const pd_plan*, const double*, double*, double*, double, double, cudaStream_t);
+template cudaError_t synth_primal<float>(const pd_plan*, float*, float*, const float*, double, double, cudaStream_t);
+template cudaError_t synth_primal<double>(const pd_plan*, double*, double*, const double*, double, double,
+                                          cudaStream_t);
 template cudaError_t norm2<float>(const pd_plan*, const float*, int64_t, double*, cudaStream_t);
 template cudaError_t norm2<double>(const pd_plan*, const double*, int64_t, double*, cudaStream_t);
 template cudaError_t scale_copy<float>(const float*, float*, int64_t, double, cudaStream_t);

@@ -136,6 +136,8 @@ struct pd_state {
     void* xt = nullptr;
     void* s = nullptr;             // [b][ny][nx]
     void* st = nullptr;            // s~ = Psi s
+    void* syn_at = nullptr;        // synthesis form: alpha~ [b][ny][nx] (alpha lives in s)
+    void* syn_u = nullptr;         // synthesis form: positivity dual u [ny][nx]
     void* v = nullptr;             // complex [M] internal order
     void* u = nullptr;             // complex grid G^T v (panel layout)
     void* y = nullptr;             // complex [M] internal order
@@ -264,6 +266,11 @@ struct SelectArgs {
     double n, p_min, p_max;
 };
 cudaError_t select_active(const pd_plan* p, pd_state* st, const SelectArgs& a, cudaStream_t s);
+// synthesis form: positivity dual and image-domain primal term; primal step on the coefficients
+template <typename R>
+cudaError_t synth_dual(const pd_plan* p, const R* xt, R* u, R* back, double sigma, double varsigma, cudaStream_t s);
+template <typename R>
+cudaError_t synth_primal(const pd_plan* p, R* alpha, R* alpha_t, const R* w, double tau, double thr, cudaStream_t s);
 cudaError_t primal_finish(const pd_plan* p, pd_state* st, cudaStream_t s);
 template <typename R>
 cudaError_t norm2(const pd_plan* p, const R* x, int64_t n, double* out, cudaStream_t s);
