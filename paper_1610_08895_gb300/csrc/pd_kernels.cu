@@ -128,6 +128,10 @@ __global__ void __launch_bounds__(SEL_NT) k_select(
         const int per = (ntiles + SEL_NT - 1) / SEL_NT;
         const int k0 = min(ntiles, tid * per), k1 = min(ntiles, k0 + per);
         int mine = 0, segs = 0, mc[4] = {0, 0, 0, 0};
+        // the flags of this thread's tiles, kept in registers for the compaction pass
+        // below (up to 128 tiles per thread; beyond that it reads tile_active back)
+        constexpr int FW = 4;
+        uint32_t onm[FW] = {0u, 0u, 0u, 0u};
         // batches of tiles whose independent loads go out together
         constexpr int TB = 8;
         for (int kb = k0; kb < k1; kb += TB) {
@@ -149,8 +153,14 @@ __global__ void __launch_bounds__(SEL_NT) k_select(
                     segs += a;
                 }
                 tile_active[tt[i]] = on;
+                const int li = kb + i - k0;
+#pragma unroll
+                for (int f = 0; f < FW; ++f)
+                    if (on && (li >> 5) == f) onm[f] |= 1u << (li & 31);
                 mine += on;
-                if (on) mc[tile_colour(tt[i], ntx)]++;
+                const int col = tile_colour(tt[i], ntx);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) mc[c] += on && col == c;
             }
         }
         int excl, sexcl, cex[4];
@@ -161,11 +171,23 @@ __global__ void __launch_bounds__(SEL_NT) k_select(
         for (int c = 0; c < 4; ++c) ctot[c] = block_excl_scan(mc[c], shi, cex[c]);
         const int q = ntiles / 4;
         for (int k = k0; k < k1; ++k) {
-            const int tt = tile_order[k];
-            if (tile_active[tt]) {
+            const int li = k - k0;
+            bool on;
+            if (li < 32 * FW) {
+                uint32_t w = onm[0];
+#pragma unroll
+                for (int f = 1; f < FW; ++f) w = (li >> 5) == f ? onm[f] : w;
+                on = (w >> (li & 31)) & 1u;
+            } else {
+                on = tile_active[tile_order[k]];
+            }
+            if (on) {
+                const int tt = tile_order[k];
                 act_tiles[excl++] = tt;
-                const int c = tile_colour(tt, ntx);
-                act_col[c * q + cex[c]++] = tt;
+                const int col = tile_colour(tt, ntx);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (col == c) act_col[c * q + cex[c]++] = tt;
             }
         }
         if (tid == 0) {
