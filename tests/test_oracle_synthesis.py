@@ -84,3 +84,19 @@ def test_synthesis_converges_to_independent_solver_solution():
     x_ref = prob.psi(a_ref)
     assert np.all(x_ref >= -1e-9)
     assert np.all(PD.block_residuals(prob, x_ref) <= prob.eps * (1 + 1e-9))
+
+
+@pytest.mark.slow
+def test_synthesis_with_the_dirac_basis_is_the_analysis_problem():
+    # with Psi = I (the Dirac basis alone) both formulations minimise ||x||_1 over the same
+    # constraint set: Algorithm 1 and the synthesis iterations reach the same minimum
+    prob, _ = tiny_problem(basis_ids=(0,), levels=1)
+    x0 = synth.start_vector(8, 8, seed=9)
+    phi2, psi2 = PD.operator_norms(prob, x0, max_iter=5000, tol=1e-13)
+    st_a, _ = PD.pd_run(prob, 8000, tau=0.49, sigma=1.0 / psi2, varsigma=1.0 / phi2, kappa=0.1,
+                        psi_norm=np.sqrt(psi2), seed=0, p_block=[1.0] * 2, p_basis=[1.0])
+    st_s, _ = SY.synthesis_run(prob, 8000, tau=0.49, sigma=1.0, varsigma=1.0 / phi2, kappa=0.1, seed=0,
+                               p_block=[1.0] * 2)
+    xs = st_s.x(prob)
+    assert np.abs(xs).sum() == pytest.approx(np.abs(st_a.x).sum(), rel=1e-4)
+    assert np.all(PD.block_residuals(prob, xs) <= prob.eps * (1 + 1e-4))
