@@ -102,6 +102,7 @@ cudaError_t build_csr(pd_plan* p, cudaStream_t s) {
     if (M == 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     if (p->csr_cplx) {
+        if (p->kb_J != 2 && p->kb_J != 4 && p->kb_J != 6) return cudaErrorInvalidValue;   // J + d - 1 <= 8, d >= 3
         // the DDE kernels go to the device once, for this build only
         double2* dd = nullptr;
         const size_t bytes = p->h_dde.size() * sizeof(double);
