@@ -82,8 +82,7 @@ def test_weighted_pd_converges_to_independent_solver_solution():
     f_pd = np.abs(wts * prob.psi_adj(st.x)).sum()
     f_ref = np.abs(wts * prob.psi_adj(x_ref)).sum()
     assert f_pd == pytest.approx(f_ref, rel=1e-4)
-    print("rel dist", np.linalg.norm(st.x - x_ref) / np.linalg.norm(x_ref))
-    assert np.linalg.norm(st.x - x_ref) / np.linalg.norm(x_ref) < 1e-4
+    assert np.linalg.norm(st.x - x_ref) / np.linalg.norm(x_ref) < 1e-4      # measured 8e-12
     # the weighted problem has another solution than the unweighted one
     x_l1 = admm_reference(prob)
     assert np.linalg.norm(x_l1 - x_ref) / np.linalg.norm(x_ref) > 1e-3
